@@ -1,0 +1,350 @@
+"""Benchmark: window-MI evaluations per second of the iSYCOS hot path on GB300.
+
+Workload (one "step"): the paper's searches over 64 synthetic pairs of FP32 series of length
+100,000 with planted linear / quadratic / sin(3X) / exp(X) segments (lengths log-uniform in
+[50, 5000], SNR in {0.5, 2, 10}, iid N(0,1) background), k = 4, window sizes 32-4096,
+sigma = 0.2 on the normalised score, noise pruning on: SYCOS_TD (Algorithm 1) and SYCOS_BU
+(Algorithm 2) over all 64 pairs, each algorithm's frontiers of all pairs merged into shared
+persistent MI launches.  The series stay resident in HBM (value); the e2e figure uploads them
+from pinned host memory and reads the found windows back inside the timed region.
+
+The JSON line follows the driver's contract; see the design doc for the roofline definition.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "window-MI evals/sec and pairwise comparisons/sec vs FP32 roofline; p50/p99 query latency"
+N_PAIRS = 64
+N_LEN = 100_000
+PARAMS = dict(k=4, s_min=32, s_max=4096, sigma=0.2, tau=0.05, pruning=1, seed=20220419)
+# lane operations per ordered pair of the brute-force method: pass 1 (two subtractions with
+# |.|, max, compare) = 5 with the predicated insertion, pass 2 (two subtractions, two
+# compares, two adds) = 6
+OPS_PER_PAIR = 11
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=N_PAIRS)
+    ap.add_argument("--length", type=int, default=N_LEN)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_pairs(rank, n_pairs, length):
+    from paper_2204_09131_gb300 import synth
+    pairs = []
+    for p in range(n_pairs):
+        x, y, _ = synth.planted_pair(2, rank * n_pairs + p, length)
+        pairs.append((x, y))
+    return pairs
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def run_step(api, ctx, ids, length):
+    xs = [a for a, _ in ids]
+    ys = [b for _, b in ids]
+    nq = len(ids)
+    found = 0
+    for mode in (0, 1):
+        res = api.isycos_search_many(ctx, xs, ys, [0] * nq, [length] * nq, dict(PARAMS, mode=mode))
+        found += sum(len(r) for r in res)
+    return found
+
+
+def flush_l2(torch, buf):
+    buf.fill_(1.0)          # 256 MiB write, larger than the 129 MB L2
+
+
+def serving_probe(api, ctx, ids, length, n_queries=200, rate_hz=None):
+    """Poisson stream of search queries over the resident pairs (reduced size)."""
+    rng = np.random.default_rng(4)
+    queries = []
+    for i in range(n_queries):
+        a, b = ids[int(rng.integers(0, len(ids)))]
+        span = int(np.exp(rng.uniform(np.log(1000), np.log(length))))
+        lo = int(rng.integers(0, length - span + 1))
+        s_max = int(2 ** rng.integers(8, 13))
+        s_max = max(64, min(s_max, span // 2))
+        queries.append((a, b, lo, lo + span, dict(PARAMS, s_max=s_max, mode=int(i % 2))))
+    # calibrate: one query's service time
+    t0 = time.perf_counter()
+    api.isycos_search(ctx, *queries[0][:4], queries[0][4])
+    t1 = time.perf_counter() - t0
+    rate = rate_hz or max(1.0, 0.7 * 32 / max(t1, 1e-4))
+    gaps = rng.exponential(1.0 / rate, n_queries)
+    tickets = []
+    start = time.perf_counter()
+    nxt = start
+    done = {}
+    for q, g in zip(queries, gaps):
+        nxt += g
+        while time.perf_counter() < nxt:
+            for t in tickets:
+                if t not in done:
+                    r = api.isycos_serve_poll(ctx, t)
+                    if r is not None:
+                        done[t] = r[1]
+            time.sleep(0.0005)
+        tickets.append(api.isycos_serve_submit(ctx, *q[:4], q[4]))
+    while len(done) < len(tickets):
+        for t in tickets:
+            if t not in done:
+                r = api.isycos_serve_poll(ctx, t)
+                if r is not None:
+                    done[t] = r[1]
+        time.sleep(0.0005)
+    wall = time.perf_counter() - start
+    lat = np.array([done[t] for t in tickets])
+    return {"queries": n_queries, "arrival_rate_hz": round(rate, 2),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "throughput_qps": round(n_queries / wall, 2)}
+
+
+def cpu_baseline(pairs, budget_s=15.0):
+    """The oracle, single thread, on a bounded sample: TD then BU (pruning on) on prefixes of
+    pair 0 until the CPU budget is spent; evals/s = windows scored / seconds."""
+    from oracle import oracle as O
+    x, y = pairs[0]
+    kw = dict(PARAMS)
+    evals, secs = 0, 0.0
+    span = 12000
+    t0 = time.perf_counter()
+    _, n1 = O.search_td(x[:span], y[:span], **kw)
+    _, n2 = O.search_bu(x[:span], y[:span], **kw)
+    secs = time.perf_counter() - t0
+    evals = n1 + n2
+    return {"value": round(evals / secs, 2), "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first "
+                      "%d points of pair 0: %d window scores in %.1f s" % (span, evals, secs)}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    pairs = make_pairs(0, 1, args.length)
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(pairs))
+    v = statistics.median([c["value"] for c in vals])
+    line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "isycos-td-bu-64x100k", "pairs": 1, "length": 12000,
+                       "k": 4, "s_min": 32, "s_max": 4096, "pruning": 1},
+            "cpu_baseline": dict(vals[-1], value=v),
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2204_09131_gb300 import api
+
+    pairs = make_pairs(rank, args.pairs, args.length)
+    ctx = api.isycos_create(local, 0)
+    ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
+    l2buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        run_step(api, ctx, ids, args.length)
+    torch.cuda.synchronize()
+
+    api.isycos_reset_stats(ctx)
+    times = []
+    found = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush_l2(torch, l2buf)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            found = run_step(api, ctx, ids, args.length)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    st = api.isycos_get_stats(ctx)
+    total_ms = sum(times)
+    windows = st["windows"]
+    pairs_cnt = st["pairs"]
+    if world > 1:
+        t = torch.tensor([total_ms, windows, pairs_cnt], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max = mx[0].item()
+        windows_all, pairs_all = t[1].item(), t[2].item()
+    else:
+        total_ms_max, windows_all, pairs_all = total_ms, windows, pairs_cnt
+    value = windows_all / (total_ms_max / 1e3)
+    pairs_per_s = pairs_all / (total_ms_max / 1e3)
+
+    # e2e: series uploaded from pinned host memory, searches, results read back.
+    e2e = None
+    if rank == 0:
+        pinned = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()) for x, y in pairs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eids = []
+        for x, y in pinned:
+            eids.append((api.isycos_put_series(ctx, x.numpy()), api.isycos_put_series(ctx, y.numpy())))
+        st0 = api.isycos_get_stats(ctx)
+        nfound = run_step(api, ctx, eids, args.length)
+        st1 = api.isycos_get_stats(ctx)
+        for a, b in eids:
+            api.isycos_drop_series(ctx, a)
+            api.isycos_drop_series(ctx, b)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": round((st1["windows"] - st0["windows"]) / dt, 2), "unit": "evals/s",
+               "h2d_bytes_per_step": int(2 * len(pairs) * args.length * 4),
+               "d2h_bytes_per_step": int(nfound * 32)}
+
+    # roofline of the dominant kernel (the batched MI kernel): algorithmic lane operations
+    # per launch over its event-timed duration, against the CUDA-core issue peak
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clocks["sm_mhz"] or 2070.0
+    peak = n_sm * 4 * 32 * f_mhz * 1e6 / 1e9        # G lane-ops / s
+    kms = st["mi_kernel_ms"]
+    achieved = (OPS_PER_PAIR * pairs_cnt) / (kms / 1e3) / 1e9 if kms > 0 else None
+    roof = {"bound": "alu", "achieved": round(achieved, 1) if achieved else None,
+            "peak": round(peak, 1), "unit": "Glane-op/s",
+            "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+            "kernel": "ksg_batched_kernel", "kernel_ms_per_step": round(kms / args.steps, 3),
+            "kernel_share_of_step": round(kms / total_ms, 4) if total_ms else None,
+            "peak_basis": "%d SMs x 4 warp-instr/clk x 32 lanes x %.0f MHz (median SM clock "
+                          "sampled during the timed region)" % (n_sm, f_mhz)}
+
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_probe(api, ctx, ids, args.length)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pairs)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "isycos-td-bu-64x100k", "pairs_per_gpu": args.pairs,
+                       "length": args.length, "k": 4, "s_min": 32, "s_max": 4096,
+                       "sigma": 0.2, "pruning": 1, "searches": "SYCOS_TD + SYCOS_BU",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "pairs_per_s": round(pairs_per_s, 1),
+            "pairs_note": "brute-force-equivalent ordered pairs m(m-1) per evaluated window",
+            "windows_per_step": int(windows_all / args.steps),
+            "found_windows_per_step": found,
+            "gpu_launches": int(st["launches"]),
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "serving": serving,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    api.isycos_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

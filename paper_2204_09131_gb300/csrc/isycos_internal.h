@@ -1,0 +1,110 @@
+// Internal declarations shared by the host runtime and the CUDA kernels of libisycos.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "isycos.h"
+
+namespace isy {
+
+constexpr int kMaxM = ISYCOS_MAX_M;
+constexpr int kMaxK = ISYCOS_MAX_K;
+constexpr int kTableN = kMaxM + 2;      // psi_fx / log_fx entries 0 .. kMaxM + 1
+constexpr int kBuckets = 15;            // size buckets: m <= 2^b, b = 0 .. 14, stored largest first
+constexpr int kPoints = 2;              // points per thread in the brute-force kernels
+constexpr int kBlockPts = 32 * kPoints; // points per warp block
+
+// One resolved window: device pointers to its first X and Y values.  32 bytes.
+struct WorkItem {
+    const float *x;
+    const float *y;
+    int32_t m;
+    int32_t out;      // index of the result in the output array (input order)
+    int64_t pts;      // offset of the window's points in the per-point arrays, or -1
+};
+
+// Work layout of one persistent launch: items sorted by size bucket, largest bucket first.
+// A job is one item (large windows, all warps of the CTA) or several items of one
+// bucket (small windows, `wpw` warps each).
+struct BucketTable {
+    int32_t total_jobs;
+    int32_t n_items;
+    int32_t item_off[kBuckets];  // first item of bucket slot q
+    int32_t count[kBuckets];     // items in bucket slot q
+    int32_t job_off[kBuckets];   // first job of bucket slot q
+    int32_t wpw[kBuckets];       // warps per item in bucket slot q
+};
+
+struct BatchArgs {
+    const WorkItem *items;
+    const BucketTable *table;
+    int32_t *queue;              // persistent work counter (zeroed before launch)
+    const long long *psi_fx;
+    const long long *log_fx;
+    isycos_mi_out *out;
+    int32_t *nx;                 // optional per-point outputs (nullptr: skip)
+    int32_t *ny;
+    int32_t *c;
+    int32_t k;
+    int32_t nt;                  // threads per CTA of the launch
+};
+
+// Device-side preparation of a window list held in device memory.
+struct PrepArgs {
+    const isycos_window *windows;
+    int64_t n_w;
+    int32_t k;
+    int32_t max_m;
+    const float *const *series_ptr;  // device table of resident series
+    const int64_t *series_len;
+    int32_t n_series;
+    int32_t nt;                      // threads per CTA of the MI launch that follows
+    WorkItem *items;                 // n_w entries (sorted output)
+    int32_t *bucket_count;           // kBuckets counters (zeroed before launch)
+    int32_t *slot_of;                // n_w scratch: bucket slot of each window or -1
+    int32_t *pos_of;                 // n_w scratch: position inside the bucket
+    BucketTable *table;
+    int32_t *status;                 // error flags (bit 0: invalid window)
+    isycos_mi_out *out;              // invalid windows get NaN results
+};
+
+// Launchers (kernels.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t batched_occupancy(int k, int nt, size_t smem, int *blocks_per_sm);
+cudaError_t set_batched_smem(int k, int nt, size_t smem);
+cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
+                         const long long *log_fx, unsigned long long *acc, int32_t *done,
+                         isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                         cudaStream_t st, int *launches);
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st, int *launches);
+cudaError_t launch_check_finite(const float *d, int64_t n, int32_t *flag, cudaStream_t st);
+
+// Bucket of a window size: smallest b with m <= 2^b; slot q = kBuckets - 1 - b (largest first).
+inline int bucket_slot(int m) {
+    int b = 0;
+    while ((1 << b) < m) ++b;
+    return kBuckets - 1 - b;
+}
+
+// Warps per item for bucket slot q in a CTA of nt threads.
+inline int warps_per_item(int q, int nt) {
+    int w = nt / 32;
+    int b = kBuckets - 1 - q;
+    int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
+    int wpw = 1;
+    while (wpw < need && wpw < w) wpw *= 2;
+    return wpw;
+}
+
+// Shared memory of a batched launch whose largest window has max_m points.
+inline size_t batched_smem(int max_m, int nt) {
+    size_t a = (size_t)max_m * 8;
+    size_t b = (size_t)nt * kPoints * 8;   // all slots of the small-window buckets
+    return a > b ? a : b;
+}
+
+// Threads per CTA chosen for a batch whose largest window has max_m points.
+inline int batched_threads(int max_m) { return max_m > 8192 ? 1024 : 256; }
+
+}  // namespace isy

@@ -1,0 +1,519 @@
+// Window-level KSG mutual information on the GPU (arXiv 2204.09131, Sec. 4.2 Eq. KSGmi,
+// Def. 4.2; counting rule of the box-assisted example of Sec. 7.1; score of Sec. 5.4).
+//
+// For a window {(x_j, y_j)}, j = 0 .. m-1, and every point i:
+//   a2  d_ij = max(|x_i - x_j|, |y_i - y_j|) (binary32, exact IEEE sub/abs/max); the
+//       k nearest neighbours are the first k points j != i in the order of (d_ij, j);
+//   a3  d_x,i, d_y,i = largest |x_i - x_j|, |y_i - y_j| over those neighbours;
+//   a4  n_x,i = #{j != i : |x_i - x_j| <= d_x,i}, n_y,i likewise, c_i = #{j : (x_j, y_j) = (x_i, y_i)};
+//   a5  S_psi = sum_i psi_fx[n_x,i] + psi_fx[n_y,i], S_log = sum_i log_fx[c_i] (int64, exact)
+//       and the scalars of isycos_mi_out in a fixed binary64 order.
+//
+// Neighbour search keeps, per point, the first k+1 entries of (d_ij, j) over ALL j of the
+// window including i itself (d_ii = 0).  Since the point itself is among those k+1 entries,
+// or all of them are at distance 0, the k+1 list minus one zero-distance entry is exactly
+// the k-neighbour set of j != i; a zero entry adds nothing to the per-dimension maxima, so
+// d_x,i and d_y,i are the maxima over the whole list and no per-pair j != i test is needed.
+// j is scanned in increasing order and an entry replaces the list's last entry only when
+// strictly closer, which realises the tie-break toward the smaller index.
+//
+// c_i: when the (k+1)-th distance is positive every duplicate of (x_i, y_i), i included, is
+// in the list, so c_i = number of zero-distance entries; otherwise a third pass counts them
+// (taken by a warp only if one of its points needs it).
+//
+// Layout: the window's values are staged in shared memory as float2 (x, y); each lane owns
+// kPoints points of a 64-point block and reads (x_j, y_j) as a broadcast, so every shared
+// load serves 32 * kPoints pairs.  Work: m (m - 1) pairs per pass; no tensor cores (the path
+// is compare-and-count work on the FP32/INT pipes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "isycos_internal.h"
+
+namespace isy {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUnroll = 4;
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Stable insertion of (d, j) into the ascending list bd/bj of K1 entries, given that d is
+// strictly smaller than the last entry: the last entry is replaced and bubbled toward the
+// front while strictly smaller than its predecessor.
+template <int K1>
+__device__ __forceinline__ void list_insert(float (&bd)[K1], int (&bj)[K1], float d, int j) {
+    bd[K1 - 1] = d;
+    bj[K1 - 1] = j;
+#pragma unroll
+    for (int r = K1 - 1; r > 0; --r) {
+        const bool sw = bd[r] < bd[r - 1];
+        const float a0 = bd[r - 1], a1 = bd[r];
+        const int b0 = bj[r - 1], b1 = bj[r];
+        bd[r - 1] = sw ? a1 : a0;
+        bd[r] = sw ? a0 : a1;
+        bj[r - 1] = sw ? b1 : b0;
+        bj[r] = sw ? b0 : b1;
+    }
+}
+
+// Canonical binary64 evaluation of the window scalars from the exact integer sums.
+__device__ __forceinline__ void write_result(isycos_mi_out *o, int k, int m, long long s_psi,
+                                             long long s_log, const long long *psi_fx,
+                                             const long long *log_fx) {
+    const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
+    const double psi_k = __dmul_rn(__ll2double_rn(psi_fx[k]), two_m32);
+    const double psi_m = __dmul_rn(__ll2double_rn(psi_fx[m]), two_m32);
+    const double inv_k = __ddiv_rn(1.0, (double)k);
+    const double mean_psi = __ddiv_rn(__dmul_rn(__ll2double_rn(s_psi), two_m32), (double)m);
+    const double mi = __dsub_rn(__dadd_rn(__dsub_rn(psi_k, inv_k), psi_m), mean_psi);
+    const double ln_m = __dmul_rn(__ll2double_rn(log_fx[m]), two_m32);
+    const double h = __dsub_rn(ln_m, __ddiv_rn(__dmul_rn(__ll2double_rn(s_log), two_m32), (double)m));
+    o->mi = mi;
+    o->h_w = h;
+    o->nmi = h > 0.0 ? __ddiv_rn(mi, h) : 0.0;
+    o->s_psi = s_psi;
+    o->s_log = s_log;
+}
+
+// One 64-point block of a window staged in shared memory `s` (m points): all of a2-a5 for
+// points base + p * 32 + lane, p < kPoints.  Adds the block's sums to acc_psi / acc_log.
+template <int K1>
+__device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, int base,
+                                          int lane, const long long *__restrict__ psi_fx,
+                                          const long long *__restrict__ log_fx,
+                                          long long &acc_psi, long long &acc_log,
+                                          int32_t *nx_out, int32_t *ny_out, int32_t *c_out) {
+    constexpr int P = kPoints;
+    const float kInf = __int_as_float(0x7f800000);
+    float xi[P], yi[P];
+    bool val[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = base + p * 32 + lane;
+        val[p] = i < m;
+        const float2 v = val[p] ? s[i] : make_float2(kInf, kInf);  // sentinel never inserts
+        xi[p] = v.x;
+        yi[p] = v.y;
+    }
+
+    // a2: first K1 entries of (d_ij, j) over all j, self included.
+    float bd[P][K1];
+    int bj[P][K1];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            bd[p][r] = kInf;
+            bj[p][r] = 0;
+        }
+    int j = 0;
+    for (; j + kUnroll <= m; j += kUnroll) {
+        float2 v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) v[u] = s[j + u];
+        float d[kUnroll][P];
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                d[u][p] = fmaxf(fabsf(xi[p] - v[u].x), fabsf(yi[p] - v[u].y));
+                any |= d[u][p] < bd[p][K1 - 1];
+            }
+        if (any) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    if (d[u][p] < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d[u][p], j + u);
+        }
+    }
+    for (; j < m; ++j) {
+        const float2 v = s[j];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float d = fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y));
+            if (d < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d, j);
+        }
+    }
+
+    // a3: per-dimension distances to the neighbours.
+    float dxm[P], dym[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        dxm[p] = 0.0f;
+        dym[p] = 0.0f;
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            const float2 v = s[bj[p][r]];
+            dxm[p] = fmaxf(dxm[p], fabsf(xi[p] - v.x));
+            dym[p] = fmaxf(dym[p], fabsf(yi[p] - v.y));
+        }
+    }
+
+    // a4: marginal counts (inclusive; the point itself is counted and removed below).
+    int cx[P], cy[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        cx[p] = 0;
+        cy[p] = 0;
+    }
+    j = 0;
+    for (; j + kUnroll <= m; j += kUnroll) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const float2 v = s[j + u];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                cx[p] += fabsf(xi[p] - v.x) <= dxm[p] ? 1 : 0;
+                cy[p] += fabsf(yi[p] - v.y) <= dym[p] ? 1 : 0;
+            }
+        }
+    }
+    for (; j < m; ++j) {
+        const float2 v = s[j];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            cx[p] += fabsf(xi[p] - v.x) <= dxm[p] ? 1 : 0;
+            cy[p] += fabsf(yi[p] - v.y) <= dym[p] ? 1 : 0;
+        }
+    }
+
+    // Multiplicity of (x_i, y_i).
+    int cc[P];
+    bool need = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        cc[p] = 0;
+#pragma unroll
+        for (int r = 0; r < K1; ++r) cc[p] += bd[p][r] == 0.0f ? 1 : 0;
+        need |= val[p] && bd[p][K1 - 1] == 0.0f;
+    }
+    if (__any_sync(kFull, need)) {
+        int dup[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) dup[p] = 0;
+        for (int jj = 0; jj < m; ++jj) {
+            const float2 v = s[jj];
+#pragma unroll
+            for (int p = 0; p < P; ++p) dup[p] += (xi[p] == v.x && yi[p] == v.y) ? 1 : 0;
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (bd[p][K1 - 1] == 0.0f) cc[p] = dup[p];
+    }
+
+    // a5: fixed-point digamma and log sums.
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!val[p]) continue;
+        const int nxv = cx[p] - 1, nyv = cy[p] - 1;
+        acc_psi += __ldg(psi_fx + nxv) + __ldg(psi_fx + nyv);
+        acc_log += __ldg(log_fx + cc[p]);
+        const int i = base + p * 32 + lane;
+        if (nx_out) {
+            nx_out[i] = nxv;
+            ny_out[i] = nyv;
+            c_out[i] = cc[p];
+        }
+    }
+}
+
+// Persistent, size-bucketed batch: CTAs take jobs from a counter; a job is one large window
+// (all warps) or several small windows of one bucket (wpw warps each).
+template <int K1, int NT>
+__global__ void __launch_bounds__(NT) ksg_batched_kernel(BatchArgs a) {
+    extern __shared__ float2 tile[];
+    constexpr int W = NT / 32;
+    __shared__ long long acc_psi[W], acc_log[W];
+    __shared__ int job_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const BucketTable *T = a.table;
+    for (;;) {
+        if (threadIdx.x == 0) job_s = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int job = job_s;
+        if (job >= T->total_jobs) break;
+        int q = 0;
+        while (q + 1 < kBuckets && job >= T->job_off[q + 1]) ++q;
+        const int wpw = T->wpw[q];
+        const int per_job = W / wpw;
+        const int slot = warp / wpw, sub = warp % wpw;
+        const int first = T->item_off[q] + (job - T->job_off[q]) * per_job;
+        const int last = T->item_off[q] + T->count[q];
+        const bool has = first + slot < last;
+        WorkItem it;
+        it.m = 0;
+        if (has) it = a.items[first + slot];
+        float2 *s = tile + (per_job == 1 ? 0 : slot * (kBlockPts * wpw));
+        if (has)
+            for (int i = sub * 32 + lane; i < it.m; i += wpw * 32) s[i] = make_float2(it.x[i], it.y[i]);
+        if (lane == 0 && sub == 0) {
+            acc_psi[slot] = 0;
+            acc_log[slot] = 0;
+        }
+        __syncthreads();
+        if (has) {
+            long long lp = 0, ll = 0;
+            int32_t *nxo = nullptr, *nyo = nullptr, *co = nullptr;
+            if (a.nx && it.pts >= 0) {
+                nxo = a.nx + it.pts;
+                nyo = a.ny + it.pts;
+                co = a.c + it.pts;
+            }
+            const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
+            for (int b = sub; b < nblk; b += wpw)
+                ksg_block<K1>(s, it.m, b * kBlockPts, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            lp = warp_sum64(lp);
+            ll = warp_sum64(ll);
+            if (lane == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc_psi[slot]), (unsigned long long)lp);
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc_log[slot]), (unsigned long long)ll);
+            }
+        }
+        __syncthreads();
+        if (has && sub == 0 && lane == 0)
+            write_result(a.out + it.out, a.k, it.m, acc_psi[slot], acc_log[slot], a.psi_fx, a.log_fx);
+    }
+}
+
+// Plain form: one window per launch; CTA b handles the blocks b*W .. b*W + W - 1 and the
+// last CTA to finish writes the result.
+template <int K1, int NT>
+__global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const long long *psi_fx,
+                                                       const long long *log_fx,
+                                                       unsigned long long *acc, int32_t *done,
+                                                       isycos_mi_out *out, int32_t *nx,
+                                                       int32_t *ny, int32_t *c) {
+    extern __shared__ float2 tile[];
+    constexpr int W = NT / 32;
+    __shared__ long long sp[W], sl[W];
+    __shared__ bool is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < it.m; i += NT) tile[i] = make_float2(it.x[i], it.y[i]);
+    __syncthreads();
+    long long lp = 0, ll = 0;
+    const int b = blockIdx.x * W + warp;
+    const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
+    if (b < nblk) ksg_block<K1>(tile, it.m, b * kBlockPts, lane, psi_fx, log_fx, lp, ll, nx, ny, c);
+    lp = warp_sum64(lp);
+    ll = warp_sum64(ll);
+    if (lane == 0) {
+        sp[warp] = lp;
+        sl[warp] = ll;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tp = 0, tl = 0;
+        for (int w = 0; w < W; ++w) {
+            tp += sp[w];
+            tl += sl[w];
+        }
+        atomicAdd(acc, (unsigned long long)tp);
+        atomicAdd(acc + 1, (unsigned long long)tl);
+        __threadfence();
+        is_last = atomicAdd(done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        const long long tp = (long long)atomicAdd(acc, 0ull);
+        const long long tl = (long long)atomicAdd(acc + 1, 0ull);
+        write_result(out, k, it.m, tp, tl, psi_fx, log_fx);
+        acc[0] = 0;
+        acc[1] = 0;
+        *done = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Device-side preparation of window lists that live in device memory.
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int dev_bucket_slot(int m) {
+    int b = 32 - __clz(m - 1);   // smallest b with m <= 2^b (m >= 2)
+    if (m <= 1) b = 0;
+    return kBuckets - 1 - b;
+}
+
+__global__ void prep_classify_kernel(PrepArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_w) return;
+    const isycos_window w = a.windows[i];
+    bool ok = w.reserved == 0 && w.xs >= 0 && w.xs < a.n_series && w.ys >= 0 &&
+              w.ys < a.n_series && w.m >= a.k + 1 && w.m <= a.max_m && w.m <= kMaxM &&
+              w.start >= 0;
+    if (ok) {
+        const int64_t nx = a.series_len[w.xs], ny = a.series_len[w.ys];
+        ok = nx > 0 && ny > 0 && w.start + w.m <= nx && w.start + w.m <= ny &&
+             a.series_ptr[w.xs] != nullptr && a.series_ptr[w.ys] != nullptr;
+    }
+    if (!ok) {
+        atomicOr(a.status, 1);
+        a.slot_of[i] = -1;
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        a.out[i].mi = nan;
+        a.out[i].h_w = nan;
+        a.out[i].nmi = nan;
+        a.out[i].s_psi = 0;
+        a.out[i].s_log = 0;
+        return;
+    }
+    const int q = dev_bucket_slot(w.m);
+    a.slot_of[i] = q;
+    a.pos_of[i] = atomicAdd(a.bucket_count + q, 1);
+}
+
+__global__ void prep_table_kernel(PrepArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    BucketTable *T = a.table;
+    const int W = a.nt / 32;
+    int items = 0, jobs = 0;
+    for (int q = 0; q < kBuckets; ++q) {
+        const int b = kBuckets - 1 - q;
+        const int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
+        int wpw = 1;
+        while (wpw < need && wpw < W) wpw *= 2;
+        const int n = a.bucket_count[q];
+        T->item_off[q] = items;
+        T->count[q] = n;
+        T->job_off[q] = jobs;
+        T->wpw[q] = wpw;
+        items += n;
+        jobs += (n + (W / wpw) - 1) / (W / wpw);
+    }
+    T->total_jobs = jobs;
+    T->n_items = items;
+}
+
+__global__ void prep_scatter_kernel(PrepArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_w) return;
+    const int q = a.slot_of[i];
+    if (q < 0) return;
+    const isycos_window w = a.windows[i];
+    WorkItem it;
+    it.x = a.series_ptr[w.xs] + w.start;
+    it.y = a.series_ptr[w.ys] + w.start;
+    it.m = w.m;
+    it.out = (int32_t)i;
+    it.pts = -1;
+    a.items[a.table->item_off[q] + a.pos_of[i]] = it;
+}
+
+__global__ void check_finite_kernel(const float *d, int64_t n, int32_t *flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) bad |= !isfinite(d[i]);
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// Kernel tables by k (K1 = k + 1).
+template <int NT>
+struct BatchedTable {
+    using Fn = void (*)(BatchArgs);
+    static Fn get(int k) {
+        switch (k) {
+            case 1: return ksg_batched_kernel<2, NT>;
+            case 2: return ksg_batched_kernel<3, NT>;
+            case 3: return ksg_batched_kernel<4, NT>;
+            case 4: return ksg_batched_kernel<5, NT>;
+            case 5: return ksg_batched_kernel<6, NT>;
+            case 6: return ksg_batched_kernel<7, NT>;
+            case 7: return ksg_batched_kernel<8, NT>;
+            case 8: return ksg_batched_kernel<9, NT>;
+        }
+        return nullptr;
+    }
+};
+
+using PlainFn = void (*)(WorkItem, int, const long long *, const long long *, unsigned long long *,
+                         int32_t *, isycos_mi_out *, int32_t *, int32_t *, int32_t *);
+constexpr int kPlainNT = 256;
+
+PlainFn plain_fn(int k) {
+    switch (k) {
+        case 1: return ksg_plain_kernel<2, kPlainNT>;
+        case 2: return ksg_plain_kernel<3, kPlainNT>;
+        case 3: return ksg_plain_kernel<4, kPlainNT>;
+        case 4: return ksg_plain_kernel<5, kPlainNT>;
+        case 5: return ksg_plain_kernel<6, kPlainNT>;
+        case 6: return ksg_plain_kernel<7, kPlainNT>;
+        case 7: return ksg_plain_kernel<8, kPlainNT>;
+        case 8: return ksg_plain_kernel<9, kPlainNT>;
+    }
+    return nullptr;
+}
+
+void (*batched_fn(int k, int nt))(BatchArgs) {
+    if (nt == 256) return BatchedTable<256>::get(k);
+    if (nt == 1024) return BatchedTable<1024>::get(k);
+    return nullptr;
+}
+
+}  // namespace
+
+cudaError_t set_batched_smem(int k, int nt, size_t smem) {
+    auto fn = batched_fn(k, nt);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t batched_occupancy(int k, int nt, size_t smem, int *blocks_per_sm) {
+    auto fn = batched_fn(k, nt);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, nt, smem);
+}
+
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st) {
+    auto fn = batched_fn(a.k, a.nt);
+    if (!fn) return cudaErrorInvalidValue;
+    fn<<<grid, a.nt, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
+                         const long long *log_fx, unsigned long long *acc, int32_t *done,
+                         isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                         cudaStream_t st, int *launches) {
+    PlainFn fn = plain_fn(k);
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)it.m * 8;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int per_cta = (kPlainNT / 32) * kBlockPts;
+    const int grid = (it.m + per_cta - 1) / per_cta;
+    fn<<<grid, kPlainNT, smem, st>>>(it, k, psi_fx, log_fx, acc, done, out, nx, ny, c);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st, int *launches) {
+    const int nt = 256;
+    const int grid = (int)((a.n_w + nt - 1) / nt);
+    if (grid > 0) prep_classify_kernel<<<grid, nt, 0, st>>>(a);
+    prep_table_kernel<<<1, 32, 0, st>>>(a);
+    if (grid > 0) prep_scatter_kernel<<<grid, nt, 0, st>>>(a);
+    if (launches) *launches += grid > 0 ? 3 : 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const float *d, int64_t n, int32_t *flag, cudaStream_t st) {
+    const int nt = 256;
+    int64_t blocks = (n + nt - 1) / nt;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<(int)blocks, nt, 0, st>>>(d, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace isy

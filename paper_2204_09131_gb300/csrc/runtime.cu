@@ -1,0 +1,681 @@
+// Host runtime of libisycos: context, resident series, window-MI entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace isy;
+
+namespace isy {
+
+isycos_status fail(isycos_ctx *ctx, isycos_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->err_mu);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+isycos_status cuda_fail(isycos_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, ISYCOS_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+isycos_status dev_reserve(isycos_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return ISYCOS_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~(size_t)255;
+    if (ctx->used.load() - b.cap + want > ctx->budget) {
+        want = (bytes + 255) & ~(size_t)255;
+        if (ctx->used.load() - b.cap + want > ctx->budget)
+            return fail(ctx, ISYCOS_E_NOMEM, "device budget exceeded: need %zu more bytes",
+                        want - b.cap);
+    }
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->used -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ISYCOS_E_NOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+    }
+    b.p = p;
+    b.cap = want;
+    ctx->used += want;
+    return ISYCOS_OK;
+}
+
+void dev_release(isycos_ctx *ctx, DevBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->used -= b.cap;
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+isycos_status host_reserve(isycos_ctx *ctx, HostBuf &b, size_t bytes) {
+    if (bytes <= b.cap) return ISYCOS_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMallocHost(&b.p, want);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost");
+    b.cap = want;
+    return ISYCOS_OK;
+}
+
+void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches,
+               int64_t batches, int64_t incr_windows) {
+    std::lock_guard<std::mutex> g(ctx->stats_mu);
+    ctx->stats.windows += windows;
+    ctx->stats.pairs += pairs;
+    ctx->stats.launches += launches;
+    ctx->stats.batches += batches;
+    ctx->stats.incr_windows += incr_windows;
+}
+
+cudaStream_t pick_stream(isycos_ctx *ctx, void *s) {
+    return s ? reinterpret_cast<cudaStream_t>(s) : ctx->stream;
+}
+
+isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k) {
+    const int64_t ns = (int64_t)ctx->series_ptr.size();
+    if (w.reserved != 0) return fail(ctx, ISYCOS_E_INVAL, "window.reserved must be 0");
+    if (w.xs < 0 || w.xs >= ns || !ctx->series_ptr[w.xs] || w.ys < 0 || w.ys >= ns ||
+        !ctx->series_ptr[w.ys])
+        return fail(ctx, ISYCOS_E_INVAL, "unknown series id (%d, %d)", w.xs, w.ys);
+    if (w.m < k + 1 || w.m > kMaxM)
+        return fail(ctx, ISYCOS_E_INVAL, "window size %d outside [k + 1 = %d, %d]", w.m, k + 1, kMaxM);
+    const int64_t n = std::min(ctx->series_len[w.xs], ctx->series_len[w.ys]);
+    if (w.start < 0 || w.start + w.m > n)
+        return fail(ctx, ISYCOS_E_INVAL, "window [%lld, %lld] outside the series (length %lld)",
+                    (long long)w.start, (long long)(w.start + w.m - 1), (long long)n);
+    return ISYCOS_OK;
+}
+
+// Build the persistent launch's bucket table for items already sorted by slot.
+static void build_table(BucketTable &T, const int32_t *count, int nt) {
+    const int W = nt / 32;
+    int items = 0, jobs = 0;
+    for (int q = 0; q < kBuckets; ++q) {
+        const int wpw = warps_per_item(q, nt);
+        T.item_off[q] = items;
+        T.count[q] = count[q];
+        T.job_off[q] = jobs;
+        T.wpw[q] = wpw;
+        items += count[q];
+        jobs += (count[q] + (W / wpw) - 1) / (W / wpw);
+    }
+    T.total_jobs = jobs;
+    T.n_items = items;
+}
+
+static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
+    int idx = nt == 1024 ? 1 : 0;
+    if (smem <= ctx->smem_set[idx]) return ISYCOS_OK;
+    for (int kk = 1; kk <= kMaxK; ++kk) {
+        cudaError_t e = set_batched_smem(kk, nt, smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
+    (void)k;
+    ctx->smem_set[idx] = smem;
+    return ISYCOS_OK;
+}
+
+static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, int jobs_hint,
+                                 int *grid) {
+    int per_sm = 0;
+    cudaError_t e = batched_occupancy(k, nt, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+    if (per_sm < 1) return fail(ctx, ISYCOS_E_INVAL, "kernel does not fit on an SM (smem %zu)", smem);
+    int g = ctx->n_sm * per_sm;
+    if (jobs_hint > 0 && jobs_hint < g) g = jobs_hint;
+    *grid = std::max(g, 1);
+    return ISYCOS_OK;
+}
+
+isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k,
+                          isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                          cudaStream_t st) {
+    if (n <= 0) return ISYCOS_OK;
+    if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
+    int max_m = 0;
+    int64_t pairs = 0, total_pts = 0;
+    int32_t count[kBuckets] = {0};
+    std::vector<int32_t> slot((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        max_m = std::max(max_m, w[i].m);
+        pairs += (int64_t)w[i].m * (w[i].m - 1);
+        slot[i] = bucket_slot(w[i].m);
+        count[slot[i]]++;
+        total_pts += w[i].m;
+    }
+    const int nt = batched_threads(max_m);
+    const size_t smem = batched_smem(max_m, nt);
+    isycos_status rc;
+    if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
+
+    // Items sorted by bucket slot (largest windows first), in pinned memory.
+    if ((rc = host_reserve(ctx, ctx->h_items, sizeof(WorkItem) * n))) return rc;
+    if ((rc = host_reserve(ctx, ctx->h_table, sizeof(BucketTable)))) return rc;
+    BucketTable &T = *reinterpret_cast<BucketTable *>(ctx->h_table.p);
+    build_table(T, count, nt);
+    int32_t fill[kBuckets];
+    for (int q = 0; q < kBuckets; ++q) fill[q] = T.item_off[q];
+    WorkItem *items = reinterpret_cast<WorkItem *>(ctx->h_items.p);
+    int64_t pts = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        WorkItem &it = items[fill[slot[i]]++];
+        it.x = ctx->series_ptr[w[i].xs] + w[i].start;
+        it.y = ctx->series_ptr[w[i].ys] + w[i].start;
+        it.m = w[i].m;
+        it.out = (int32_t)i;
+        it.pts = nx ? pts : -1;
+        pts += w[i].m;
+    }
+
+    if ((rc = dev_reserve(ctx, ctx->d_items, sizeof(WorkItem) * n))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_table, sizeof(BucketTable)))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_queue, 256))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_out, sizeof(isycos_mi_out) * n))) return rc;
+    if (nx) {
+        if ((rc = dev_reserve(ctx, ctx->d_nx, 4 * total_pts))) return rc;
+        if ((rc = dev_reserve(ctx, ctx->d_ny, 4 * total_pts))) return rc;
+        if ((rc = dev_reserve(ctx, ctx->d_c, 4 * total_pts))) return rc;
+    }
+    cudaError_t e;
+    e = cudaMemcpyAsync(ctx->d_items.p, items, sizeof(WorkItem) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_table.p, &T, sizeof(BucketTable), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue.p, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "staging the window list");
+
+    int grid;
+    if ((rc = launch_grid(ctx, k, nt, smem, T.total_jobs, &grid))) return rc;
+    BatchArgs a;
+    a.items = reinterpret_cast<const WorkItem *>(ctx->d_items.p);
+    a.table = reinterpret_cast<const BucketTable *>(ctx->d_table.p);
+    a.queue = reinterpret_cast<int32_t *>(ctx->d_queue.p);
+    a.psi_fx = ctx->d_psi_fx;
+    a.log_fx = ctx->d_log_fx;
+    a.out = reinterpret_cast<isycos_mi_out *>(ctx->d_out.p);
+    a.nx = nx ? reinterpret_cast<int32_t *>(ctx->d_nx.p) : nullptr;
+    a.ny = nx ? reinterpret_cast<int32_t *>(ctx->d_ny.p) : nullptr;
+    a.c = nx ? reinterpret_cast<int32_t *>(ctx->d_c.p) : nullptr;
+    a.k = k;
+    a.nt = nt;
+    e = cudaEventRecord(ctx->ev_start, st);
+    if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_stop, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
+    e = cudaMemcpyAsync(out, ctx->d_out.p, sizeof(isycos_mi_out) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && nx) {
+        e = cudaMemcpyAsync(nx, ctx->d_nx.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ny, ctx->d_ny.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c, ctx->d_c.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev_start, ctx->ev_stop);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel");
+    add_stats(ctx, n, pairs, 1, 1, 0);
+    {
+        std::lock_guard<std::mutex> g(ctx->stats_mu);
+        ctx->stats.mi_kernel_ms += ms;
+        ctx->stats.mi_kernel_launches += 1;
+    }
+    return ISYCOS_OK;
+}
+
+static isycos_status sync_series_table(isycos_ctx *ctx, cudaStream_t st) {
+    if (!ctx->series_dirty) return ISYCOS_OK;
+    const size_t ns = std::max<size_t>(ctx->series_ptr.size(), 1);
+    isycos_status rc;
+    if ((rc = dev_reserve(ctx, ctx->d_series_ptr, sizeof(float *) * ns))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_series_len, sizeof(int64_t) * ns))) return rc;
+    if (!ctx->series_ptr.empty()) {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_series_ptr.p, ctx->series_ptr.data(),
+                                        sizeof(float *) * ctx->series_ptr.size(),
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->d_series_len.p, ctx->series_len.data(),
+                                sizeof(int64_t) * ctx->series_len.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "series table upload");
+    }
+    ctx->series_dirty = false;
+    return ISYCOS_OK;
+}
+
+static void build_tables(std::vector<long long> &psi_fx, std::vector<long long> &log_fx) {
+    // psi(1) = -gamma, psi(n + 1) = psi(n) + 1/n (binary64 forward recurrence); values
+    // rounded to the nearest multiple of 2^-32.
+    const double gamma = 0.57721566490153286060651209008240243;
+    psi_fx.assign(kTableN, 0);
+    log_fx.assign(kTableN, 0);
+    double psi = -gamma;
+    for (int n = 1; n < kTableN; ++n) {
+        psi_fx[n] = llround(ldexp(psi, 32));
+        log_fx[n] = llround(ldexp(log((double)n), 32));
+        psi = psi + 1.0 / (double)n;
+    }
+}
+
+}  // namespace isy
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+
+extern "C" {
+
+void isycos_params_default(isycos_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->k = 4;
+    p->score_kind = 0;
+    p->sigma = 0.2;
+    p->tau = -1.0;   /* sigma / 4 */
+    p->s_min = 32;
+    p->s_max = 256;
+    p->delta_td = 0;
+    p->delta_bu = 0;
+    p->h = 8;
+    p->t_max_idle = 3;
+    p->p = 3;
+    p->mode = 0;
+    p->pruning = 0;
+    p->max_steps = 10000;
+    p->seed = 0;
+}
+
+isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budget_bytes) {
+    if (!out) return ISYCOS_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ISYCOS_E_CUDA;
+    }
+    if (device < 0 || device >= ndev) return ISYCOS_E_INVAL;
+    isycos_ctx *ctx = new isycos_ctx();
+    ctx->device = device;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_stop);
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return ISYCOS_E_CUDA;
+    }
+    ctx->budget = mem_budget_bytes ? mem_budget_bytes : (uint64_t)(0.9 * (double)free_b);
+    build_tables(ctx->h_psi_fx, ctx->h_log_fx);
+    void *p = nullptr, *q = nullptr;
+    e = cudaMalloc(&p, sizeof(long long) * kTableN);
+    if (e == cudaSuccess) e = cudaMalloc(&q, sizeof(long long) * kTableN);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p, ctx->h_psi_fx.data(), sizeof(long long) * kTableN, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(q, ctx->h_log_fx.data(), sizeof(long long) * kTableN, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p) cudaFree(p);
+        if (q) cudaFree(q);
+        cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return ISYCOS_E_CUDA;
+    }
+    ctx->d_psi_fx = reinterpret_cast<long long *>(p);
+    ctx->d_log_fx = reinterpret_cast<long long *>(q);
+    ctx->used += 2 * sizeof(long long) * kTableN;
+    *out = ctx;
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_destroy(isycos_ctx *ctx) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    for (float *p : ctx->series_ptr)
+        if (p) cudaFree(p);
+    DevBuf *bufs[] = {&ctx->d_series_ptr, &ctx->d_series_len, &ctx->d_items, &ctx->d_table,
+                      &ctx->d_queue, &ctx->d_out, &ctx->d_nx, &ctx->d_ny, &ctx->d_c,
+                      &ctx->d_slot, &ctx->d_pos, &ctx->d_bcount, &ctx->d_status,
+                      &ctx->d_plain_acc};
+    for (DevBuf *b : bufs) dev_release(ctx, *b);
+    if (ctx->h_items.p) cudaFreeHost(ctx->h_items.p);
+    if (ctx->h_table.p) cudaFreeHost(ctx->h_table.p);
+    cudaFree(ctx->d_psi_fx);
+    cudaFree(ctx->d_log_fx);
+    cudaEventDestroy(ctx->ev_start);
+    cudaEventDestroy(ctx->ev_stop);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return ISYCOS_OK;
+}
+
+const char *isycos_last_error(const isycos_ctx *ctx) {
+    if (!ctx) return "null context";
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    return ctx->err.c_str();
+}
+
+isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, int32_t on_device,
+                                int32_t *series_id) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (!data || n < 1 || !series_id) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments");
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    const size_t bytes = sizeof(float) * (size_t)n;
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!isfinite(data[i]))
+                return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld is not finite", (long long)i);
+    }
+    if (ctx->used.load() + bytes > ctx->budget)
+        return fail(ctx, ISYCOS_E_NOMEM, "put_series: device budget exceeded");
+    float *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ISYCOS_E_NOMEM, "put_series: cudaMalloc(%zu) failed", bytes);
+    }
+    ctx->used += bytes;
+    e = cudaMemcpyAsync(d, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        ctx->stream);
+    int32_t bad = 0;
+    if (e == cudaSuccess && on_device) {
+        isycos_status rc = dev_reserve(ctx, ctx->d_status, 256);
+        if (rc) {
+            cudaFree(d);
+            ctx->used -= bytes;
+            return rc;
+        }
+        int32_t *flag = reinterpret_cast<int32_t *>(ctx->d_status.p) + 8;
+        e = cudaMemsetAsync(flag, 0, 4, ctx->stream);
+        if (e == cudaSuccess) e = launch_check_finite(d, n, flag, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess || bad) {
+        cudaFree(d);
+        ctx->used -= bytes;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "put_series");
+        return fail(ctx, ISYCOS_E_INVAL, "put_series: the series holds non-finite values");
+    }
+    int32_t id = -1;
+    for (size_t i = 0; i < ctx->series_ptr.size(); ++i)
+        if (!ctx->series_ptr[i]) {
+            id = (int32_t)i;
+            break;
+        }
+    if (id < 0) {
+        id = (int32_t)ctx->series_ptr.size();
+        ctx->series_ptr.push_back(nullptr);
+        ctx->series_len.push_back(0);
+    }
+    ctx->series_ptr[id] = d;
+    ctx->series_len[id] = n;
+    ctx->series_dirty = true;
+    *series_id = id;
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_drop_series(isycos_ctx *ctx, int32_t series_id) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    if (series_id < 0 || series_id >= (int32_t)ctx->series_ptr.size() || !ctx->series_ptr[series_id])
+        return fail(ctx, ISYCOS_E_NOTFOUND, "unknown series %d", series_id);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->series_ptr[series_id]);
+    ctx->used -= sizeof(float) * (size_t)ctx->series_len[series_id];
+    ctx->series_ptr[series_id] = nullptr;
+    ctx->series_len[series_id] = 0;
+    ctx->series_dirty = true;
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_series_info(isycos_ctx *ctx, int32_t series_id, const float **device_ptr,
+                                 int64_t *n) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (series_id < 0 || series_id >= (int32_t)ctx->series_ptr.size() || !ctx->series_ptr[series_id])
+        return fail(ctx, ISYCOS_E_NOTFOUND, "unknown series %d", series_id);
+    if (device_ptr) *device_ptr = ctx->series_ptr[series_id];
+    if (n) *n = ctx->series_len[series_id];
+    return ISYCOS_OK;
+}
+
+static isycos_status host_windows(isycos_ctx *ctx, const isycos_window *windows, int64_t n_w,
+                                  int32_t k, std::vector<HostWindow> &hw) {
+    if (k < 1 || k > kMaxK) return fail(ctx, ISYCOS_E_INVAL, "k = %d outside [1, %d]", k, kMaxK);
+    if (n_w < 0 || (n_w > 0 && !windows)) return fail(ctx, ISYCOS_E_INVAL, "bad window list");
+    hw.resize((size_t)n_w);
+    for (int64_t i = 0; i < n_w; ++i) {
+        isycos_status rc = check_window(ctx, windows[i], k);
+        if (rc) return fail(ctx, rc, "window %lld: %s", (long long)i, ctx->err.c_str());
+        hw[i] = HostWindow{windows[i].xs, windows[i].ys, windows[i].start, windows[i].m};
+    }
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_mi_windows(isycos_ctx *ctx, const isycos_window *windows, int64_t n_w,
+                                int32_t k, isycos_mi_out *out, void *cuda_stream) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_w > 0 && !out) return fail(ctx, ISYCOS_E_INVAL, "out is NULL");
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    std::vector<HostWindow> hw;
+    isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
+    if (rc) return rc;
+    return engine_eval(ctx, hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
+                       pick_stream(ctx, cuda_stream));
+}
+
+isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *windows,
+                                       int64_t n_w, int32_t k, isycos_mi_out *out, int32_t *nx,
+                                       int32_t *ny, int32_t *c, void *cuda_stream) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_w > 0 && (!out || !nx || !ny || !c))
+        return fail(ctx, ISYCOS_E_INVAL, "output arrays must not be NULL");
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    std::vector<HostWindow> hw;
+    isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
+    if (rc) return rc;
+    return engine_eval(ctx, hw.data(), n_w, k, out, nx, ny, c, pick_stream(ctx, cuda_stream));
+}
+
+isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_windows,
+                                       int64_t n_w, int32_t k, int32_t max_m,
+                                       isycos_mi_out *d_out, void *cuda_stream) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (k < 1 || k > kMaxK) return fail(ctx, ISYCOS_E_INVAL, "k = %d outside [1, %d]", k, kMaxK);
+    if (max_m < k + 1 || max_m > kMaxM)
+        return fail(ctx, ISYCOS_E_INVAL, "max_m = %d outside [k + 1, %d]", max_m, kMaxM);
+    if (n_w < 0 || n_w > INT32_MAX / 2 || (n_w > 0 && (!d_windows || !d_out)))
+        return fail(ctx, ISYCOS_E_INVAL, "bad window list");
+    if (n_w == 0) return ISYCOS_OK;
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    isycos_status rc;
+    if ((rc = sync_series_table(ctx, st))) return rc;
+    const int nt = batched_threads(max_m);
+    const size_t smem = batched_smem(max_m, nt);
+    if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_items, sizeof(WorkItem) * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_slot, 4 * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_pos, 4 * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_bcount, 4 * kBuckets + 64))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_table, sizeof(BucketTable)))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_queue, 256))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_status, 256))) return rc;
+    PrepArgs pa;
+    pa.windows = d_windows;
+    pa.n_w = n_w;
+    pa.k = k;
+    pa.max_m = max_m;
+    pa.series_ptr = reinterpret_cast<const float *const *>(ctx->d_series_ptr.p);
+    pa.series_len = reinterpret_cast<const int64_t *>(ctx->d_series_len.p);
+    pa.n_series = (int32_t)ctx->series_ptr.size();
+    pa.nt = nt;
+    pa.items = reinterpret_cast<WorkItem *>(ctx->d_items.p);
+    pa.bucket_count = reinterpret_cast<int32_t *>(ctx->d_bcount.p);
+    pa.slot_of = reinterpret_cast<int32_t *>(ctx->d_slot.p);
+    pa.pos_of = reinterpret_cast<int32_t *>(ctx->d_pos.p);
+    pa.table = reinterpret_cast<BucketTable *>(ctx->d_table.p);
+    pa.status = reinterpret_cast<int32_t *>(ctx->d_status.p);
+    pa.out = d_out;
+    cudaError_t e = cudaMemsetAsync(ctx->d_bcount.p, 0, 4 * kBuckets, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue.p, 0, 4, st);
+    int launches = 0;
+    if (e == cudaSuccess) e = launch_prep(pa, st, &launches);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "window preparation");
+    int grid;
+    if ((rc = launch_grid(ctx, k, nt, smem, 0, &grid))) return rc;
+    BatchArgs a;
+    a.items = pa.items;
+    a.table = pa.table;
+    a.queue = reinterpret_cast<int32_t *>(ctx->d_queue.p);
+    a.psi_fx = ctx->d_psi_fx;
+    a.log_fx = ctx->d_log_fx;
+    a.out = d_out;
+    a.nx = a.ny = a.c = nullptr;
+    a.k = k;
+    a.nt = nt;
+    e = launch_batched(a, grid, smem, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
+    add_stats(ctx, n_w, 0, launches + 1, 1, 0);
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_device_status(isycos_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device status");
+    if (!ctx->d_status.p) return ISYCOS_OK;
+    int32_t flag = 0;
+    e = cudaMemcpyAsync(&flag, ctx->d_status.p, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device status");
+    if (flag & 1) return fail(ctx, ISYCOS_E_INVAL, "an asynchronous call received invalid windows");
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *windows,
+                                      int64_t n_w, int32_t k, isycos_mi_out *out,
+                                      void *cuda_stream) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_w > 0 && !out) return fail(ctx, ISYCOS_E_INVAL, "out is NULL");
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    std::vector<HostWindow> hw;
+    isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
+    if (rc) return rc;
+    if (n_w == 0) return ISYCOS_OK;
+    cudaStream_t st = pick_stream(ctx, cuda_stream);
+    if ((rc = dev_reserve(ctx, ctx->d_out, sizeof(isycos_mi_out) * n_w))) return rc;
+    if (!ctx->d_plain_acc.p) {
+        if ((rc = dev_reserve(ctx, ctx->d_plain_acc, 256))) return rc;
+        cudaError_t e = cudaMemset(ctx->d_plain_acc.p, 0, 256);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    }
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(ctx->d_plain_acc.p);
+    int32_t *done = reinterpret_cast<int32_t *>(acc + 2);
+    isycos_mi_out *d_out = reinterpret_cast<isycos_mi_out *>(ctx->d_out.p);
+    int launches = 0;
+    int64_t pairs = 0;
+    for (int64_t i = 0; i < n_w; ++i) {
+        WorkItem it;
+        it.x = ctx->series_ptr[hw[i].xs] + hw[i].start;
+        it.y = ctx->series_ptr[hw[i].ys] + hw[i].start;
+        it.m = hw[i].m;
+        it.out = (int32_t)i;
+        it.pts = -1;
+        pairs += (int64_t)it.m * (it.m - 1);
+        cudaError_t e = launch_plain(it, k, ctx->d_psi_fx, ctx->d_log_fx, acc, done, d_out + i,
+                                     nullptr, nullptr, nullptr, st, &launches);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "plain MI kernel launch");
+    }
+    cudaError_t e = cudaMemcpyAsync(out, d_out, sizeof(isycos_mi_out) * n_w, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plain MI kernel");
+    add_stats(ctx, n_w, pairs, launches, n_w, 0);
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_get_stats(isycos_ctx *ctx, isycos_stats *out) {
+    if (!ctx || !out) return ISYCOS_E_INVAL;
+    std::lock_guard<std::mutex> g(ctx->stats_mu);
+    *out = ctx->stats;
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_reset_stats(isycos_ctx *ctx) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    std::lock_guard<std::mutex> g(ctx->stats_mu);
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int64_t *log_fx) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_max < 0 || n_max >= kTableN || !psi_fx || !log_fx)
+        return fail(ctx, ISYCOS_E_INVAL, "tables: n_max must be in [0, %d]", kTableN - 1);
+    for (int32_t n = 0; n <= n_max; ++n) {
+        psi_fx[n] = ctx->h_psi_fx[n];
+        log_fx[n] = ctx->h_log_fx[n];
+    }
+    return ISYCOS_OK;
+}
+
+isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    switch (option) {
+        case ISYCOS_OPT_KERNEL:
+            if (value < 0 || value > 2) break;
+            ctx->opt_kernel = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_INCREMENTAL:
+            if (value < 0 || value > 2) break;
+            ctx->opt_incremental = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_SERVE_SLOTS:
+            if (value < 1 || value > 1 << 20) break;
+            ctx->serve_slots = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_SERVE_QUEUE:
+            if (value < 1 || value > 1 << 24) break;
+            ctx->serve_queue = (int)value;
+            return ISYCOS_OK;
+        default:
+            return fail(ctx, ISYCOS_E_INVAL, "unknown option %d", option);
+    }
+    return fail(ctx, ISYCOS_E_INVAL, "option %d: value %lld out of range", option, (long long)value);
+}
+
+}  // extern "C"

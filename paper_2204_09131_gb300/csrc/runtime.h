@@ -1,0 +1,108 @@
+// Host runtime of libisycos: the context, resident series, device work buffers and the
+// batch engine that turns window lists into persistent MI launches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "isycos.h"
+#include "isycos_internal.h"
+
+namespace isy {
+
+class Server;
+
+// A growable device buffer whose bytes count against the context's budget.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+// A growable pinned host buffer.
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+// One window of a resident pair as the engine sees it (already validated).
+struct HostWindow {
+    int32_t xs, ys;
+    int64_t start;
+    int32_t m;
+};
+
+}  // namespace isy
+
+struct isycos_ctx {
+    int device = 0;
+    int n_sm = 0;
+    uint64_t budget = 0;
+    std::atomic<uint64_t> used{0};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    mutable std::mutex err_mu;
+
+    // 2^-32 fixed-point digamma and log tables (host copy and device copy).
+    std::vector<long long> h_psi_fx, h_log_fx;
+    long long *d_psi_fx = nullptr, *d_log_fx = nullptr;
+
+    // Resident series.
+    std::vector<float *> series_ptr;
+    std::vector<int64_t> series_len;
+    isy::DevBuf d_series_ptr, d_series_len;
+    bool series_dirty = true;
+
+    // Engine work buffers (guarded by engine_mu).
+    std::mutex engine_mu;
+    isy::DevBuf d_items, d_table, d_queue, d_out, d_nx, d_ny, d_c;
+    isy::DevBuf d_slot, d_pos, d_bcount, d_status, d_plain_acc;
+    isy::HostBuf h_items, h_table;
+    size_t smem_set[2] = {0, 0};   // dynamic smem attribute set per (nt = 256, 1024), all k
+
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // MI kernel timing
+    isycos_stats stats{};
+    std::mutex stats_mu;
+
+    // Options.
+    int opt_kernel = 0;
+    int opt_incremental = 1;
+    int serve_slots = 64;
+    int serve_queue = 100000;
+
+    isy::Server *server = nullptr;
+};
+
+namespace isy {
+
+// Error helpers: record a message on the context and return the status.
+isycos_status fail(isycos_ctx *ctx, isycos_status st, const char *fmt, ...);
+isycos_status cuda_fail(isycos_ctx *ctx, cudaError_t e, const char *what);
+
+// Device buffer management with budget accounting.
+isycos_status dev_reserve(isycos_ctx *ctx, DevBuf &b, size_t bytes);
+void dev_release(isycos_ctx *ctx, DevBuf &b);
+isycos_status host_reserve(isycos_ctx *ctx, HostBuf &b, size_t bytes);
+
+// Validation of a window against the resident series (host side).
+isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k);
+
+// Evaluate n windows (validated) on `st`, synchronously; results in input order into the
+// host array `out`.  Per-point arrays (host) are optional.  Caller holds engine_mu.
+isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k,
+                          isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                          cudaStream_t st);
+
+void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches,
+               int64_t batches, int64_t incr_windows);
+
+cudaStream_t pick_stream(isycos_ctx *ctx, void *s);
+
+// Stop and free the serving thread of a context (serve.cu).
+void serve_shutdown(isycos_ctx *ctx);
+
+}  // namespace isy

@@ -1,0 +1,234 @@
+"""Parity of the CUDA window-MI path with the CPU oracle (GPU).
+
+The bar: per-point integers (n_x, n_y, c) and the integer sums S_psi, S_log bit-exact; the
+binary64 scalars mi, h_w, nmi within 1e-12 (the path evaluates them in the same fixed order
+from the same exact sums, so they agree to the last bit in practice; the north-star
+tolerance is 1e-5).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2204_09131_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api
+    assert torch.cuda.is_available()
+    c = api.Context(0)
+    yield c.h
+    c.close()
+
+
+def _api():
+    from paper_2204_09131_gb300 import api
+    return api
+
+
+def _check_points(ctx, x, y, starts, sizes, k):
+    api = _api()
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    w = api.windows_array(xs, ys, starts, sizes)
+    out, nx, ny, c = api.isycos_mi_windows_points(ctx, w, k)
+    off = 0
+    for i, (s, m) in enumerate(zip(starts, sizes)):
+        r = O.ksg_window(x[s:s + m], y[s:s + m], k)
+        assert np.array_equal(nx[off:off + m], r["nx"]), (m, k, "nx")
+        assert np.array_equal(ny[off:off + m], r["ny"]), (m, k, "ny")
+        assert np.array_equal(c[off:off + m], r["c"]), (m, k, "c")
+        assert out["s_psi"][i] == r["s_psi"] and out["s_log"][i] == r["s_log"], (m, k)
+        assert abs(out["mi"][i] - r["mi"]) <= TOL, (m, k, out["mi"][i], r["mi"])
+        assert abs(out["h_w"][i] - r["h_w"]) <= TOL and abs(out["nmi"][i] - r["nmi"]) <= TOL
+        off += m
+    # the batched result without per-point outputs is the same
+    out2 = api.isycos_mi_windows(ctx, w, k)
+    assert np.array_equal(out2["s_psi"], out["s_psi"]) and np.array_equal(out2["mi"], out["mi"])
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+    return out
+
+
+def test_tables_equal_the_oracle(ctx):
+    api = _api()
+    psi, lg = api.isycos_tables(ctx, api.MAX_M + 1)
+    opsi, olg = O.fixed_tables(api.MAX_M + 1)
+    assert np.array_equal(psi, opsi) and np.array_equal(lg, olg)
+
+
+# sizes around every bucket edge and the 64-point block edge, plus a ragged tail
+EDGE_SIZES = [5, 9, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 255, 256, 257, 511, 513, 1000,
+              2047, 2049]
+
+
+@pytest.mark.parametrize("k", [1, 3, 4, 6, 8])
+def test_points_bucket_edges(ctx, k):
+    n = 6000
+    x, y = synth.gaussian_pair(synth.seed_for(200, k), n, 0.5)
+    sizes = [m for m in EDGE_SIZES if m >= k + 1]
+    starts = [(97 * i) % (n - m) for i, m in enumerate(sizes)]
+    _check_points(ctx, x, y, starts, sizes, k)
+
+
+@pytest.mark.parametrize("k", [3, 4, 6])
+def test_points_heavy_ties(ctx, k):
+    # quantised to 0.1 (cfg 5 shape) and to a coarse 0.5 grid: many equal distances and
+    # duplicate points, so the tie-break and the duplicate count matter
+    n = 5000
+    x, y = synth.gaussian_pair(synth.seed_for(201, k), n, 0.7)
+    for step_inv in (10.0, 2.0):
+        xq, yq = synth.quantize(x, step_inv), synth.quantize(y, step_inv)
+        sizes = [k + 1, 33, 64, 200, 700, 1500]
+        starts = [13 * i for i in range(len(sizes))]
+        _check_points(ctx, xq, yq, starts, sizes, k)
+
+
+def test_degenerate_windows(ctx):
+    # all points identical; identical x only; identical y only; Y = X; Y = -X
+    m = 150
+    base = synth.normal(synth.seed_for(202, 0), m).astype(np.float32)
+    cases = [(np.full(m, 1.5, np.float32), np.full(m, -2.0, np.float32)),
+             (np.full(m, 3.0, np.float32), base),
+             (base, np.zeros(m, np.float32)),
+             (base, base.copy()),
+             (base, -base)]
+    for x, y in cases:
+        _check_points(ctx, x, y, [0, 7], [m, m - 7], 4)
+
+
+def test_closed_form_y_equals_x(ctx):
+    api = _api()
+    from scipy.special import digamma
+    x = synth.normal(synth.seed_for(203, 0), 4096).astype(np.float32)
+    out = _check_points(ctx, x, x.copy(), [0], [4096], 4)
+    assert abs(out["mi"][0] - (digamma(4096) - digamma(4) - 0.25)) < 1e-8
+
+
+def test_stride1_sweep_planted_pair(ctx):
+    """Every window of size 32, 64 and 128 at stride 1 of the n = 2000 planted pair:
+    5,779 windows (40,210,720 ordered pairs), bit-exact sums against the oracle."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    wins = synth.stride_windows(len(x), [32, 64, 128])
+    assert len(wins) == 5779
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    w = api.windows_array(xs, ys, [s for s, _ in wins], [m for _, m in wins])
+    assert int((w["m"].astype(np.int64) * (w["m"] - 1)).sum()) == 40210720
+    out = api.isycos_mi_windows(ctx, w, 4)
+    for i, (s, m) in enumerate(wins):
+        r = O.ksg_window(x[s:s + m], y[s:s + m], 4, points=False)
+        assert out["s_psi"][i] == r["s_psi"] and out["s_log"][i] == r["s_log"], (s, m)
+        assert abs(out["mi"][i] - r["mi"]) <= TOL and abs(out["nmi"][i] - r["nmi"]) <= TOL
+    # plain one-window-per-launch form gives the same results
+    sub = w[::37]
+    plain = api.isycos_mi_windows_plain(ctx, sub, 4)
+    assert np.array_equal(plain["s_psi"], out["s_psi"][::37])
+    assert np.array_equal(plain["mi"], out["mi"][::37])
+
+
+def test_largest_windows_sampled_points(ctx):
+    """Windows of the largest sizes (16384, 8192, 4096, 4095) in one batch, checked on sampled
+    points (the oracle computes one point in O(m)) and, for m = 4096, on the whole window."""
+    api = _api()
+    n = 40000
+    x, y, _ = synth.planted_pair(5, 0, n)
+    xq, yq = synth.quantize(x), synth.quantize(y)
+    for xx, yy in ((x, y), (xq, yq)):
+        sizes = [16384, 8192, 4096, 4095, 64]
+        starts = [0, 16384, 30000, 1234, 39000]
+        xs = api.isycos_put_series(ctx, xx)
+        ys = api.isycos_put_series(ctx, yy)
+        w = api.windows_array(xs, ys, starts, sizes)
+        out, nx, ny, c = api.isycos_mi_windows_points(ctx, w, 6)
+        off = 0
+        rng = np.random.default_rng(7)
+        for s, m in zip(starts, sizes):
+            pts = np.unique(np.concatenate([[0, m - 1], rng.integers(0, m, 40)]))
+            for i in pts:
+                r = O.ksg_point(xx[s:s + m], yy[s:s + m], 6, int(i))
+                assert (nx[off + i], ny[off + i], c[off + i]) == (r["nx"], r["ny"], r["c"]), (m, i)
+            off += m
+        r = O.ksg_window(xx[30000:34096], yy[30000:34096], 6, points=False)
+        assert out["s_psi"][2] == r["s_psi"] and abs(out["mi"][2] - r["mi"]) <= TOL
+        api.isycos_drop_series(ctx, xs)
+        api.isycos_drop_series(ctx, ys)
+
+
+def test_device_path_matches_host_path(ctx):
+    import torch
+    api = _api()
+    x, y, _ = synth.planted_pair(2, 1, 30000)
+    xs = api.isycos_put_series(ctx, torch.from_numpy(x).cuda())
+    ys = api.isycos_put_series(ctx, torch.from_numpy(y).cuda())
+    rng = np.random.default_rng(3)
+    sizes = rng.integers(5, 3000, 500)
+    starts = [int(rng.integers(0, 30000 - m)) for m in sizes]
+    w = api.windows_array(xs, ys, starts, sizes)
+    host = api.isycos_mi_windows(ctx, w, 4)
+    dw = torch.from_numpy(w.view(np.uint8)).cuda()
+    dout = torch.empty(len(w) * 40, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    api.isycos_mi_windows_device(ctx, dw, len(w), 4, 3000, dout, st)
+    api.isycos_device_status(ctx, st)
+    dev = dout.cpu().numpy().view(api.MI_OUT_DTYPE)
+    assert np.array_equal(dev["s_psi"], host["s_psi"]) and np.array_equal(dev["mi"], host["mi"])
+    # an invalid window is flagged on the device and its result is NaN
+    bad = w[:3].copy()
+    bad["start"][1] = 29999
+    dw2 = torch.from_numpy(bad.view(np.uint8)).cuda()
+    dout2 = torch.zeros(3 * 40, dtype=torch.uint8, device="cuda")
+    api.isycos_mi_windows_device(ctx, dw2, 3, 4, 3000, dout2, st)
+    with pytest.raises(api.IsycosError):
+        api.isycos_device_status(ctx, st)
+    r2 = dout2.cpu().numpy().view(api.MI_OUT_DTYPE)
+    assert np.isnan(r2["mi"][1]) and r2["s_psi"][0] == host["s_psi"][0]
+    api.isycos_device_status(ctx, st)    # the flag was cleared
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    api = _api()
+    x = synth.normal(1, 100).astype(np.float32)
+    xs = api.isycos_put_series(ctx, x)
+    for starts, sizes, k in (([0], [4], 4), ([97], [5], 4), ([-1], [10], 4), ([0], [16385], 4),
+                             ([0], [10], 9), ([0], [10], 0)):
+        w = api.windows_array(xs, xs, starts, sizes)
+        with pytest.raises(api.IsycosError) as e:
+            api.isycos_mi_windows(ctx, w, k)
+        assert e.value.status == api.E_INVAL
+    w = api.windows_array(xs, xs + 99, [0], [10])
+    with pytest.raises(api.IsycosError):
+        api.isycos_mi_windows(ctx, w, 4)
+    empty = api.isycos_mi_windows(ctx, api.windows_array(xs, xs, [], []), 4)
+    assert empty.shape == (0,)
+    bad = x.copy()
+    bad[5] = np.nan
+    with pytest.raises(api.IsycosError):
+        api.isycos_put_series(ctx, bad)
+    import torch
+    bad_dev = torch.from_numpy(bad).cuda()
+    bad_dev[5] = float("inf")
+    with pytest.raises(api.IsycosError):
+        api.isycos_put_series(ctx, bad_dev)
+    api.isycos_drop_series(ctx, xs)
+
+
+def test_stats_count_windows_and_pairs(ctx):
+    api = _api()
+    x = synth.normal(9, 1000).astype(np.float32)
+    xs = api.isycos_put_series(ctx, x)
+    api.isycos_reset_stats(ctx)
+    w = api.windows_array(xs, xs, [0, 10, 20], [100, 200, 50])
+    api.isycos_mi_windows(ctx, w, 4)
+    s = api.isycos_get_stats(ctx)
+    assert s["windows"] == 3 and s["pairs"] == 100 * 99 + 200 * 199 + 50 * 49
+    assert s["launches"] == 1 and s["mi_kernel_launches"] == 1 and s["mi_kernel_ms"] > 0
+    api.isycos_drop_series(ctx, xs)

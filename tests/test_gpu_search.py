@@ -1,0 +1,228 @@
+"""Search and serving on the GPU against the oracle's sequential searches (GPU).
+
+isycos_search batches window scores (a whole TD layer grid, a whole BU ring) and replays the
+sequential decisions; the selected windows must equal the oracle's Algorithm 1 / Algorithm 2
+(with and without the Sec. 6 pruning) exactly, and the scores of the selected windows within
+1e-12.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2204_09131_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api
+    assert torch.cuda.is_available()
+    c = api.Context(0)
+    yield c.h
+    c.close()
+
+
+def _api():
+    from paper_2204_09131_gb300 import api
+    return api
+
+
+def _same(got, ref):
+    g = [(int(a), int(b)) for a, b in zip(got["t_s"], got["t_e"])]
+    r = [(a, b) for a, b, _, _ in ref]
+    assert g == r, (g, r)
+    for (a, b, sc, mi), gs, gm in zip(ref, got["score"], got["mi"]):
+        assert abs(gs - sc) <= 1e-12 and abs(gm - mi) <= 1e-12
+
+
+PARAMS = [
+    dict(mode=0, pruning=0), dict(mode=0, pruning=1),
+    dict(mode=1, pruning=0), dict(mode=1, pruning=1),
+    dict(mode=0, pruning=1, score_kind=1, sigma=0.5, tau=0.1),
+    dict(mode=1, pruning=1, score_kind=1, sigma=0.5, tau=0.1, seed=5),
+    dict(mode=0, delta_td=24, s_min=40, s_max=200),          # delta does not divide s_w
+    dict(mode=1, delta_bu=5, h=3, t_max_idle=1, seed=77),
+]
+
+
+@pytest.mark.parametrize("extra", PARAMS, ids=lambda d: ",".join("%s=%s" % kv for kv in d.items()))
+def test_search_matches_oracle_planted_pair(ctx, extra):
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, seed=11)
+    kw.update(extra)
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+    okw = dict(kw)
+    mode = okw.pop("mode")
+    ref, _ = (O.search_td if mode == 0 else O.search_bu)(x, y, **okw)
+    _same(got, ref)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_search_subrange_and_quantised(ctx, mode):
+    api = _api()
+    x, y, _ = synth.planted_pair(2, 3, 12000, len_lo=50, len_hi=1500)
+    x, y = synth.quantize(x), synth.quantize(y)
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    kw = dict(k=3, s_min=32, s_max=512, sigma=0.15, pruning=1, seed=2)
+    got = api.isycos_search(ctx, xs, ys, 1000, 9000, dict(kw, mode=mode))
+    ref, _ = (O.search_td if mode == 0 else O.search_bu)(x, y, t_begin=1000, t_end=9000, **kw)
+    _same(got, ref)
+
+
+def test_search_many_equals_single_searches(ctx):
+    api = _api()
+    ids = []
+    for p in range(4):
+        x, y, _ = synth.planted_pair(2, p, 8000, len_lo=50, len_hi=1000)
+        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    for mode in (0, 1):
+        prm = dict(k=4, s_min=32, s_max=512, mode=mode, pruning=1, seed=4)
+        many = api.isycos_search_many(ctx, [a for a, _ in ids], [b for _, b in ids], [0] * 4,
+                                      [8000] * 4, prm)
+        for (a, b), got in zip(ids, many):
+            one = api.isycos_search(ctx, a, b, 0, 8000, prm)
+            assert np.array_equal(one, got)
+
+
+def test_search_rejects_bad_params(ctx):
+    api = _api()
+    x = synth.normal(3, 500).astype(np.float32)
+    xs = api.isycos_put_series(ctx, x)
+    for bad in (dict(s_min=4, k=4), dict(s_min=64, s_max=32), dict(s_max=20000), dict(mode=3),
+                dict(k=9, s_min=32)):
+        with pytest.raises(api.IsycosError) as e:
+            api.isycos_search(ctx, xs, xs, 0, 500, bad)
+        assert e.value.status == api.E_INVAL
+    with pytest.raises(api.IsycosError):
+        api.isycos_search(ctx, xs, xs, 0, 501, {})
+    with pytest.raises(api.IsycosError) as e:
+        api.isycos_search(ctx, xs, 12345, 0, 100, {})
+    assert e.value.status == api.E_NOTFOUND
+
+
+def test_search_truncation_reports_needed(ctx):
+    import ctypes
+    api = _api()
+    x, y = synth.planted_small_pair()
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    full = api.isycos_search(ctx, xs, ys, 0, 2000, dict(k=4, s_min=32, s_max=256))
+    assert len(full) >= 2
+    out = np.empty(1, dtype=api.RESULT_DTYPE)
+    n = ctypes.c_int64()
+    p = api.isycos_params_default(k=4, s_min=32, s_max=256)
+    st = api.lib().isycos_search(ctx, xs, ys, 0, 2000, ctypes.byref(p), out.ctypes.data, 1,
+                                 ctypes.byref(n))
+    assert st == api.E_TRUNC and n.value == len(full)
+
+
+def _serve_all(ctx, queries, params):
+    api = _api()
+    tickets = [api.isycos_serve_submit(ctx, *q, params) for q in queries]
+    res = {}
+    deadline = time.time() + 300
+    while len(res) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t in res:
+                continue
+            r = api.isycos_serve_poll(ctx, t)
+            if r is not None:
+                res[t] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    return [res[t] for t in tickets]
+
+
+def test_serving_same_alone_and_in_the_mix(ctx):
+    api = _api()
+    pairs = []
+    for p in range(6):
+        x, y, _ = synth.planted_pair(4, p, 10000, len_lo=50, len_hi=2000)
+        pairs.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    queries = []
+    rng = np.random.default_rng(1)
+    for i in range(24):
+        a, b = pairs[i % 6]
+        lo = int(rng.integers(0, 5000))
+        hi = int(rng.integers(lo + 600, 10000))
+        queries.append((a, b, lo, hi))
+    for mode in (0, 1):
+        prm = dict(k=4, s_min=32, s_max=512, mode=mode, pruning=1, seed=9)
+        mixed = _serve_all(ctx, queries, prm)
+        for q, (wins, lat) in zip(queries, mixed):
+            alone = api.isycos_search(ctx, *q, prm)
+            assert np.array_equal(alone, wins)
+            assert lat > 0
+    s = api.isycos_get_stats(ctx)
+    assert s["queries_done"] >= 48
+
+
+def test_serving_concurrent_submitters_and_cancel(ctx):
+    api = _api()
+    x, y, _ = synth.planted_pair(4, 9, 20000)
+    a, b = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    prm = dict(k=4, s_min=32, s_max=1024, mode=0)
+    expect = api.isycos_search(ctx, a, b, 0, 20000, prm)
+    out = {}
+
+    def worker(i):
+        t = api.isycos_serve_submit(ctx, a, b, 0, 20000, prm)
+        while True:
+            r = api.isycos_serve_poll(ctx, t)
+            if r is not None:
+                out[i] = r[0]
+                return
+            time.sleep(0.001)
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert len(out) == 4 and all(np.array_equal(v, expect) for v in out.values())
+    # cancel a query: its poll reports E_CANCELED (whether it was queued or running)
+    t = api.isycos_serve_submit(ctx, a, b, 0, 20000, dict(prm, mode=1))
+    api.isycos_serve_cancel(ctx, t)
+    deadline = time.time() + 60
+    while time.time() < deadline:
+        try:
+            r = api.isycos_serve_poll(ctx, t)
+        except api.IsycosError as e:
+            assert e.status == api.E_CANCELED
+            break
+        if r is not None:      # finished before the cancel reached it
+            break
+        time.sleep(0.001)
+    with pytest.raises(api.IsycosError) as e:
+        api.isycos_serve_poll(ctx, 987654321)
+    assert e.value.status == api.E_NOTFOUND
+
+
+def test_serving_admission_under_a_small_budget():
+    """A context whose budget leaves room for one query's work buffers at a time (each TD
+    query here needs about 180 KB: 2,501 windows of the s_w = 32 layer) still completes every
+    query, one after another, with the same results."""
+    api = _api()
+    x, y, _ = synth.planted_pair(4, 11, 20000)
+    c = api.Context(0, mem_budget_bytes=(2 * 20000 * 4) + 2 * 8 * 16386 + 250_000)
+    try:
+        a, b = api.isycos_put_series(c.h, x), api.isycos_put_series(c.h, y)
+        prm = dict(k=4, s_min=32, s_max=256, mode=0)
+        res = _serve_all(c.h, [(a, b, 0, 20000)] * 3, prm)
+        ref = api.isycos_search(c.h, a, b, 0, 20000, prm)
+        assert all(np.array_equal(r[0], ref) for r in res)
+    finally:
+        c.close()
