@@ -249,6 +249,31 @@ isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int
 #define ISYCOS_OPT_SERVE_QUEUE 4   /* serving: most queries waiting (default 100000)        */
 isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
 
+/* Window MI that allocates nothing.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code running under a runtime that owns
+ * all device memory (a framework's caching allocator, a process held to a fixed device
+ * budget it hands out itself) and latency-critical loops where cudaMalloc / cudaFree would
+ * synchronise the device.  It needs no context and evaluates the same MI as
+ * isycos_mi_windows_device with the same persistent kernel, for windows of ONE pair:
+ *   d_x, d_y : device arrays of n float32 values (finite; not checked here)
+ *   d_starts : device array of n_w window starts (int64); d_sizes: n_w sizes (int32)
+ *   k, max_m : as for isycos_mi_windows_device (max_m bounds every size)
+ *   d_out    : device array of n_w results, input order
+ * Its work memory (window items, bucket table, counters; about 2.6 MiB) is one static
+ * device array, and its tables are static device arrays: every GPU that loads the library
+ * holds them until the process exits.  The first call on a device (with that device
+ * current) resolves the array's address with cudaGetSymbolAddress and uploads the tables,
+ * so it should come before any stream capture.  Calls share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU race.  Asynchronous on cuda_stream;
+ * windows outside [0, n) or with m < k + 1 or m > max_m get NaN results.
+ * Errors: E_INVAL (k, max_m, NULL pointers, or n_w > ISYCOS_NOALLOC_MAX_WINDOWS, the size
+ * of the static scratch), E_CUDA. */
+#define ISYCOS_NOALLOC_MAX_WINDOWS 65536
+isycos_status isycos_mi_windows_noalloc(const float *d_x, const float *d_y, int64_t n,
+                                        const int64_t *d_starts, const int32_t *d_sizes,
+                                        int64_t n_w, int32_t k, int32_t max_m,
+                                        isycos_mi_out *d_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,7 @@ SIGNATURES = {
     "isycos_reset_stats": (_I32, [_VP]),
     "isycos_tables": (_I32, [_VP, _I32, _VP, _VP]),
     "isycos_set_option": (_I32, [_VP, _I32, _I64]),
+    "isycos_mi_windows_noalloc": (_I32, [_VP, _VP, _I64, _VP, _VP, _I64, _I32, _I32, _VP, _VP]),
 }
 
 _lib = None
