@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--length", type=int, default=N_LEN)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--kernel-case", default=None,
+                    help="time one MI batch instead of the searches: td4096, td1024, td256, "
+                         "ring (BU-ring sized windows), mix (all TD layers)")
+    ap.add_argument("--case-pairs", type=int, default=8)
+    ap.add_argument("--plain", action="store_true", help="also time the one-window-per-launch form")
     return ap.parse_args()
 
 
@@ -117,13 +122,18 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+SPLIT = {"td_s": 0.0, "bu_s": 0.0}
+
+
 def run_step(api, ctx, ids, length):
     xs = [a for a, _ in ids]
     ys = [b for _, b in ids]
     nq = len(ids)
     found = 0
-    for mode in (0, 1):
+    for mode, key in ((0, "td_s"), (1, "bu_s")):
+        t0 = time.perf_counter()
         res = api.isycos_search_many(ctx, xs, ys, [0] * nq, [length] * nq, dict(PARAMS, mode=mode))
+        SPLIT[key] += time.perf_counter() - t0
         found += sum(len(r) for r in res)
     return found
 
@@ -219,10 +229,105 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def case_windows(name, ids, length, rng):
+    """Window lists of one MI batch shaped like the searches' frontiers."""
+    starts, sizes, xs, ys = [], [], [], []
+
+    def grid(m):
+        d = max(5, m // 4)
+        for a, b in ids:
+            for t in range(0, length - m + 1, d):
+                xs.append(a); ys.append(b); starts.append(t); sizes.append(m)
+
+    if name.startswith("td") and name[2:].isdigit():
+        grid(int(name[2:]))
+    elif name == "mix":
+        m = 4096
+        while m >= 32:
+            grid(m)
+            m //= 2
+    elif name == "chain":
+        for a, b in ids:
+            for t in range(0, 200 * 16, 16):
+                xs.append(a); ys.append(b); starts.append(t); sizes.append(2048)
+    elif name == "ring":
+        for a, b in ids:
+            for _ in range(2000):
+                m = int(np.exp(rng.uniform(np.log(32), np.log(1024))))
+                t = int(rng.integers(0, length - m))
+                xs.append(a); ys.append(b); starts.append(t); sizes.append(m)
+    else:
+        raise SystemExit("unknown kernel case %r" % name)
+    from paper_2204_09131_gb300 import api
+    w = np.zeros(len(starts), dtype=api.WINDOW_DTYPE)
+    w["xs"], w["ys"], w["start"], w["m"] = xs, ys, starts, sizes
+    return w
+
+
+def kernel_case(args):
+    """One persistent MI launch on a fixed window list, timed by the library's CUDA events."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api
+    pairs = make_pairs(0, args.case_pairs, args.length)
+    ctx = api.isycos_create(0, 0)
+    ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
+    w = case_windows(args.kernel_case, ids, args.length, np.random.default_rng(5))
+    for _ in range(args.warmup):
+        api.isycos_mi_windows(ctx, w, 4)
+    api.isycos_reset_stats(ctx)
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            api.isycos_mi_windows(ctx, w, 4)
+    st = api.isycos_get_stats(ctx)
+    ms = st["mi_kernel_ms"] / args.steps
+    pairs_per_launch = st["pairs"] / args.steps
+    clocks = clk.summary()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    f = clocks["sm_mhz"] or 2070.0
+    peak = n_sm * 4 * 32 * f * 1e6
+    ach = OPS_PER_PAIR * pairs_per_launch / (ms / 1e3)
+    line = {"kernel_case": args.kernel_case, "windows": int(len(w)), "ms_per_launch": round(ms, 4),
+            "evals_per_s": round(len(w) / (ms / 1e3), 1),
+            "pairs_per_s": round(pairs_per_launch / (ms / 1e3), 1),
+            "roofline": {"bound": "alu", "achieved": round(ach / 1e9, 1), "peak": round(peak / 1e9, 1),
+                         "unit": "Glane-op/s", "frac": round(ach / peak, 4)},
+            "clocks": clocks}
+    if args.kernel_case == "chain":
+        # the same windows through the incremental kernel, one chain per pair
+        t_inc = 0.0
+        api.isycos_reset_stats(ctx)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            for a, b in ids:
+                sel = (w["xs"] == a)
+                api.isycos_mi_chain(ctx, a, b, w["start"][sel], w["m"][sel], 4)
+            t_inc += time.perf_counter() - t0
+        st2 = api.isycos_get_stats(ctx)
+        line["incremental"] = {"s_per_pass": round(t_inc / args.steps, 4),
+                               "full_points_frac": round(st2["incr_full_points"] / max(1, int(w["m"].sum()) * args.steps), 4)}
+    if args.plain:
+        sub = w[: max(1, min(len(w), 2000))]
+        t0 = time.perf_counter()
+        api.isycos_mi_windows_plain(ctx, sub, 4)
+        t_plain = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        api.isycos_mi_windows(ctx, sub, 4)
+        t_batch = time.perf_counter() - t0
+        line["plain_vs_batched"] = {"windows": int(len(sub)), "plain_s": round(t_plain, 4),
+                                    "batched_s": round(t_batch, 4)}
+    print(json.dumps(line), flush=True)
+    api.isycos_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.kernel_case:
+        return kernel_case(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -246,6 +351,7 @@ def main():
     torch.cuda.synchronize()
 
     api.isycos_reset_stats(ctx)
+    SPLIT["td_s"] = SPLIT["bu_s"] = 0.0
     times = []
     found = 0
     with ClockSampler(local) as clk:
@@ -262,6 +368,7 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
     st = api.isycos_get_stats(ctx)
+    split = {k: round(v * 1e3 / args.steps, 2) for k, v in SPLIT.items()}
     total_ms = sum(times)
     windows = st["windows"]
     pairs_cnt = st["pairs"]
@@ -336,6 +443,8 @@ def main():
             "pairs_note": "brute-force-equivalent ordered pairs m(m-1) per evaluated window",
             "windows_per_step": int(windows_all / args.steps),
             "found_windows_per_step": found,
+            "ms_per_step_by_search": {"td": split["td_s"], "bu": split["bu_s"]},
+            "incremental_windows_per_step": int(st["incr_windows"] / args.steps),
             "gpu_launches": int(st["launches"]),
             "roofline": roof, "clocks": clocks, "e2e": e2e, "serving": serving,
             "cpu_baseline": cpu,

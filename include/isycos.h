@@ -118,9 +118,12 @@ typedef struct {
     int64_t launches;       /* kernels launched by the library                        */
     int64_t batches;        /* batched evaluations (one or more launches each)        */
     int64_t incr_windows;   /* windows evaluated by the incremental update            */
+    int64_t incr_full_points; /* points whose neighbours the incremental update searched
+                               again in full (the rest took +-1 count updates)       */
     int64_t queries_done;   /* served queries completed                               */
-    double mi_kernel_ms;    /* device time of the batched MI kernels, CUDA events on
-                               the launching stream (synchronous calls only)          */
+    double mi_kernel_ms;    /* device busy time of the batched MI kernels: the union of
+                               their [start, stop] intervals (CUDA events on each
+                               launching stream; concurrent launches counted once)    */
     int64_t mi_kernel_launches; /* launches timed in mi_kernel_ms                      */
 } isycos_stats;
 
@@ -165,7 +168,10 @@ isycos_status isycos_mi_windows(isycos_ctx *ctx, const isycos_window *windows, i
                                 int32_t k, isycos_mi_out *out, void *cuda_stream);
 
 /* As isycos_mi_windows, with both arrays in device memory.  Asynchronous on cuda_stream:
- * the call enqueues validation, bucketing and the persistent MI kernel and returns.
+ * the call enqueues validation, bucketing and the persistent MI kernel and returns.  Its
+ * work buffers belong to the context: two such calls must not overlap on different streams
+ * (calls on one stream are ordered), and dropping a series that a pending call reads is an
+ * error of the caller.
  *   max_m : an upper bound of the windows' sizes (sizes the kernel's shared memory)
  * Invalid windows are detected on the device: their results are NaN and the next call
  * of isycos_device_status() reports E_INVAL. */
@@ -194,6 +200,20 @@ isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *win
 isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *windows,
                                       int64_t n_w, int32_t k, isycos_mi_out *out,
                                       void *cuda_stream);
+
+/* Incremental window MI (Sec. 7.1, influenced regions, Lemmas 3-6): evaluates the windows
+ * [starts[i], starts[i] + sizes[i] - 1], i = 0 .. n_steps - 1, of one pair in order,
+ * deriving each window's neighbour state from the previous window's by the removed and
+ * added points: a point keeps its neighbours unless a removed or added point lies in its
+ * influenced region (the closed square of half-side eps_i around it), in which case its
+ * neighbours are searched again; marginal counts change by one for each removed or added
+ * point inside its influenced marginal regions.  Results equal isycos_mi_windows bit for
+ * bit.  A long sequence is cut into segments (at least 16 windows each) that run in
+ * parallel, each starting from scratch.  Host arrays, synchronous.
+ * Errors: as isycos_mi_windows. */
+isycos_status isycos_mi_chain(isycos_ctx *ctx, int32_t xs, int32_t ys, const int64_t *starts,
+                              const int32_t *sizes, int64_t n_steps, int32_t k,
+                              isycos_mi_out *out, void *cuda_stream);
 
 /* Correlation search on one pair (Sec. 3, the SYCOS problem): all non-overlapping windows
  * [t_s, t_e] inside [t_begin, t_end) with s_min <= size <= s_max whose score >= sigma, found

@@ -66,7 +66,8 @@ class isycos_result_window(ctypes.Structure):
 class isycos_stats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("batches", ctypes.c_int64),
-                ("incr_windows", ctypes.c_int64), ("queries_done", ctypes.c_int64),
+                ("incr_windows", ctypes.c_int64), ("incr_full_points", ctypes.c_int64),
+                ("queries_done", ctypes.c_int64),
                 ("mi_kernel_ms", ctypes.c_double), ("mi_kernel_launches", ctypes.c_int64)]
 
 
@@ -99,6 +100,7 @@ SIGNATURES = {
     "isycos_device_status": (_I32, [_VP, _VP]),
     "isycos_mi_windows_points": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP, _VP, _VP, _VP]),
     "isycos_mi_windows_plain": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP]),
+    "isycos_mi_chain": (_I32, [_VP, _I32, _I32, _VP, _VP, _I64, _I32, _VP, _VP]),
     "isycos_search": (_I32, [_VP, _I32, _I32, _I64, _I64, ctypes.POINTER(isycos_params), _VP,
                              _I64, ctypes.POINTER(_I64)]),
     "isycos_search_many": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(isycos_params),
@@ -258,6 +260,15 @@ def isycos_mi_windows_plain(ctx, windows: np.ndarray, k: int, stream=None) -> np
     out = np.empty(windows.shape[0], dtype=MI_OUT_DTYPE)
     _check(ctx, lib().isycos_mi_windows_plain(ctx, _ptr(windows), windows.shape[0], k, _ptr(out),
                                               _stream(stream)))
+    return out
+
+
+def isycos_mi_chain(ctx, xs: int, ys: int, starts, sizes, k: int, stream=None) -> np.ndarray:
+    starts = np.ascontiguousarray(starts, dtype=np.int64)
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    out = np.empty(starts.shape[0], dtype=MI_OUT_DTYPE)
+    _check(ctx, lib().isycos_mi_chain(ctx, xs, ys, _ptr(starts), _ptr(sizes), starts.shape[0], k,
+                                      _ptr(out), _stream(stream)))
     return out
 
 

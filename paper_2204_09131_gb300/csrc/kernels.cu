@@ -228,7 +228,7 @@ __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, i
 // Persistent, size-bucketed batch: CTAs take jobs from a counter; a job is one large window
 // (all warps) or several small windows of one bucket (wpw warps each).
 template <int K1, int NT>
-__global__ void __launch_bounds__(NT) ksg_batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(BatchArgs a) {
     extern __shared__ float2 tile[];
     constexpr int W = NT / 32;
     __shared__ long long acc_psi[W], acc_log[W];
@@ -463,7 +463,10 @@ void (*batched_fn(int k, int nt))(BatchArgs) {
 cudaError_t set_batched_smem(int k, int nt, size_t smem) {
     auto fn = batched_fn(k, nt);
     if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // let the whole unified L1 / shared array serve shared memory (more resident CTAs)
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 cudaError_t batched_occupancy(int k, int nt, size_t smem, int *blocks_per_sm) {

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "runtime.h"
@@ -126,6 +127,7 @@ static void build_table(BucketTable &T, const int32_t *count, int nt) {
 }
 
 static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
     int idx = nt == 1024 ? 1 : 0;
     if (smem <= ctx->smem_set[idx]) return ISYCOS_OK;
     for (int kk = 1; kk <= kMaxK; ++kk) {
@@ -140,16 +142,24 @@ static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
 static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, int jobs_hint,
                                  int *grid) {
     int per_sm = 0;
-    cudaError_t e = batched_occupancy(k, nt, smem, &per_sm);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+    const uint64_t key = ((uint64_t)k << 48) | ((uint64_t)nt << 32) | (uint64_t)smem;
+    std::lock_guard<std::mutex> g(ctx->launch_mu);
+    auto it = ctx->occupancy.find(key);
+    if (it != ctx->occupancy.end()) {
+        per_sm = it->second;
+    } else {
+        cudaError_t e = batched_occupancy(k, nt, smem, &per_sm);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+        ctx->occupancy[key] = per_sm;
+    }
     if (per_sm < 1) return fail(ctx, ISYCOS_E_INVAL, "kernel does not fit on an SM (smem %zu)", smem);
-    int g = ctx->n_sm * per_sm;
-    if (jobs_hint > 0 && jobs_hint < g) g = jobs_hint;
-    *grid = std::max(g, 1);
+    int gsz = ctx->n_sm * per_sm;
+    if (jobs_hint > 0 && jobs_hint < gsz) gsz = jobs_hint;
+    *grid = std::max(gsz, 1);
     return ISYCOS_OK;
 }
 
-isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k,
+isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                           isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
                           cudaStream_t st) {
     if (n <= 0) return ISYCOS_OK;
@@ -157,7 +167,8 @@ isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k
     int max_m = 0;
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
-    std::vector<int32_t> slot((size_t)n);
+    std::vector<int32_t> &slot = L.h_slot;
+    slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         max_m = std::max(max_m, w[i].m);
         pairs += (int64_t)w[i].m * (w[i].m - 1);
@@ -170,14 +181,18 @@ isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k
     isycos_status rc;
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
 
-    // Items sorted by bucket slot (largest windows first), in pinned memory.
-    if ((rc = host_reserve(ctx, ctx->h_items, sizeof(WorkItem) * n))) return rc;
-    if ((rc = host_reserve(ctx, ctx->h_table, sizeof(BucketTable)))) return rc;
-    BucketTable &T = *reinterpret_cast<BucketTable *>(ctx->h_table.p);
+    // One pinned staging block: the bucket table, then the items sorted by bucket slot
+    // (largest windows first); one host-to-device copy.
+    const size_t tab_bytes = (sizeof(BucketTable) + 255) & ~(size_t)255;
+    const size_t stage_bytes = tab_bytes + sizeof(WorkItem) * n;
+    if ((rc = host_reserve(ctx, L.h_items, stage_bytes))) return rc;
+    if ((rc = host_reserve(ctx, L.h_table, sizeof(isycos_mi_out) * n))) return rc;
+    unsigned char *stage = reinterpret_cast<unsigned char *>(L.h_items.p);
+    BucketTable &T = *reinterpret_cast<BucketTable *>(stage);
     build_table(T, count, nt);
     int32_t fill[kBuckets];
     for (int q = 0; q < kBuckets; ++q) fill[q] = T.item_off[q];
-    WorkItem *items = reinterpret_cast<WorkItem *>(ctx->h_items.p);
+    WorkItem *items = reinterpret_cast<WorkItem *>(stage + tab_bytes);
     int64_t pts = 0;
     for (int64_t i = 0; i < n; ++i) {
         WorkItem &it = items[fill[slot[i]]++];
@@ -189,57 +204,93 @@ isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k
         pts += w[i].m;
     }
 
-    if ((rc = dev_reserve(ctx, ctx->d_items, sizeof(WorkItem) * n))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_table, sizeof(BucketTable)))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_queue, 256))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_out, sizeof(isycos_mi_out) * n))) return rc;
+    if ((rc = dev_reserve(ctx, L.d_items, stage_bytes))) return rc;
+    if ((rc = dev_reserve(ctx, L.d_queue, 256))) return rc;
+    if ((rc = dev_reserve(ctx, L.d_out, sizeof(isycos_mi_out) * n))) return rc;
     if (nx) {
-        if ((rc = dev_reserve(ctx, ctx->d_nx, 4 * total_pts))) return rc;
-        if ((rc = dev_reserve(ctx, ctx->d_ny, 4 * total_pts))) return rc;
-        if ((rc = dev_reserve(ctx, ctx->d_c, 4 * total_pts))) return rc;
+        if ((rc = dev_reserve(ctx, L.d_nx, 4 * total_pts))) return rc;
+        if ((rc = dev_reserve(ctx, L.d_ny, 4 * total_pts))) return rc;
+        if ((rc = dev_reserve(ctx, L.d_c, 4 * total_pts))) return rc;
     }
-    cudaError_t e;
-    e = cudaMemcpyAsync(ctx->d_items.p, items, sizeof(WorkItem) * n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->d_table.p, &T, sizeof(BucketTable), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue.p, 0, 4, st);
+    cudaError_t e = cudaMemcpyAsync(L.d_items.p, stage, stage_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.d_queue.p, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "staging the window list");
 
     int grid;
     if ((rc = launch_grid(ctx, k, nt, smem, T.total_jobs, &grid))) return rc;
     BatchArgs a;
-    a.items = reinterpret_cast<const WorkItem *>(ctx->d_items.p);
-    a.table = reinterpret_cast<const BucketTable *>(ctx->d_table.p);
-    a.queue = reinterpret_cast<int32_t *>(ctx->d_queue.p);
+    a.items = reinterpret_cast<const WorkItem *>(reinterpret_cast<unsigned char *>(L.d_items.p) + tab_bytes);
+    a.table = reinterpret_cast<const BucketTable *>(L.d_items.p);
+    a.queue = reinterpret_cast<int32_t *>(L.d_queue.p);
     a.psi_fx = ctx->d_psi_fx;
     a.log_fx = ctx->d_log_fx;
-    a.out = reinterpret_cast<isycos_mi_out *>(ctx->d_out.p);
-    a.nx = nx ? reinterpret_cast<int32_t *>(ctx->d_nx.p) : nullptr;
-    a.ny = nx ? reinterpret_cast<int32_t *>(ctx->d_ny.p) : nullptr;
-    a.c = nx ? reinterpret_cast<int32_t *>(ctx->d_c.p) : nullptr;
+    a.out = reinterpret_cast<isycos_mi_out *>(L.d_out.p);
+    a.nx = nx ? reinterpret_cast<int32_t *>(L.d_nx.p) : nullptr;
+    a.ny = nx ? reinterpret_cast<int32_t *>(L.d_ny.p) : nullptr;
+    a.c = nx ? reinterpret_cast<int32_t *>(L.d_c.p) : nullptr;
     a.k = k;
     a.nt = nt;
-    e = cudaEventRecord(ctx->ev_start, st);
+    e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_stop, st);
+    if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
-    e = cudaMemcpyAsync(out, ctx->d_out.p, sizeof(isycos_mi_out) * n, cudaMemcpyDeviceToHost, st);
+    isycos_mi_out *h_out = reinterpret_cast<isycos_mi_out *>(L.h_table.p);
+    e = cudaMemcpyAsync(h_out, L.d_out.p, sizeof(isycos_mi_out) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && nx) {
-        e = cudaMemcpyAsync(nx, ctx->d_nx.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ny, ctx->d_ny.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c, ctx->d_c.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(nx, L.d_nx.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ny, L.d_ny.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c, L.d_c.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    float ms = 0.0f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev_start, ctx->ev_stop);
+    float t0 = 0.0f, t1 = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ctx->ev_ref, L.ev_start);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev_ref, L.ev_stop);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel");
+    memcpy(out, h_out, sizeof(isycos_mi_out) * n);
     add_stats(ctx, n, pairs, 1, 1, 0);
     {
+        // kernel intervals on the device timeline (lanes may overlap); their union is the
+        // kernel's busy time reported by isycos_get_stats
         std::lock_guard<std::mutex> g(ctx->stats_mu);
-        ctx->stats.mi_kernel_ms += ms;
+        ctx->kernel_iv.push_back({t0, t1});
         ctx->stats.mi_kernel_launches += 1;
     }
     return ISYCOS_OK;
+}
+
+isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out) {
+    while ((int)ctx->lanes.size() <= i) {
+        Lane *L = new Lane();
+        cudaError_t e = cudaSuccess;
+        if (ctx->lanes.empty()) {
+            L->stream = ctx->stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+            L->own_stream = true;
+        }
+        if (e == cudaSuccess) e = cudaEventCreate(&L->ev_start);
+        if (e == cudaSuccess) e = cudaEventCreate(&L->ev_stop);
+        if (e != cudaSuccess) {
+            delete L;
+            return cuda_fail(ctx, e, "lane creation");
+        }
+        ctx->lanes.push_back(L);
+    }
+    *out = ctx->lanes[i];
+    return ISYCOS_OK;
+}
+
+static void free_lane(isycos_ctx *ctx, Lane *L) {
+    DevBuf *bufs[] = {&L->d_items, &L->d_queue, &L->d_out, &L->d_nx, &L->d_ny, &L->d_c,
+                      &L->d_chain_desc, &L->d_chain_steps, &L->d_chain_state,
+                      &L->d_chain_recomp, &L->d_chain_out};
+    for (DevBuf *b : bufs) dev_release(ctx, *b);
+    if (L->h_items.p) cudaFreeHost(L->h_items.p);
+    if (L->h_table.p) cudaFreeHost(L->h_table.p);
+    if (L->ev_start) cudaEventDestroy(L->ev_start);
+    if (L->ev_stop) cudaEventDestroy(L->ev_stop);
+    if (L->own_stream) cudaStreamDestroy(L->stream);
+    delete L;
 }
 
 static isycos_status sync_series_table(isycos_ctx *ctx, cudaStream_t st) {
@@ -319,8 +370,6 @@ isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budge
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_start);
-    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_stop);
     size_t free_b = 0, total_b = 0;
     if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) {
@@ -346,6 +395,20 @@ isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budge
     ctx->d_psi_fx = reinterpret_cast<long long *>(p);
     ctx->d_log_fx = reinterpret_cast<long long *>(q);
     ctx->used += 2 * sizeof(long long) * kTableN;
+    if (cudaEventCreate(&ctx->ev_ref) != cudaSuccess || cudaEventRecord(ctx->ev_ref, ctx->stream) != cudaSuccess ||
+        cudaEventSynchronize(ctx->ev_ref) != cudaSuccess) {
+        isycos_destroy(ctx);
+        return ISYCOS_E_CUDA;
+    }
+    {
+        unsigned hw = std::thread::hardware_concurrency();
+        ctx->max_lanes = (int)std::max(1u, std::min(8u, hw / 2));
+        Lane *L0 = nullptr;
+        if (get_lane(ctx, 0, &L0) != ISYCOS_OK) {
+            isycos_destroy(ctx);
+            return ISYCOS_E_CUDA;
+        }
+    }
     *out = ctx;
     return ISYCOS_OK;
 }
@@ -357,17 +420,18 @@ isycos_status isycos_destroy(isycos_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (float *p : ctx->series_ptr)
         if (p) cudaFree(p);
-    DevBuf *bufs[] = {&ctx->d_series_ptr, &ctx->d_series_len, &ctx->d_items, &ctx->d_table,
-                      &ctx->d_queue, &ctx->d_out, &ctx->d_nx, &ctx->d_ny, &ctx->d_c,
-                      &ctx->d_slot, &ctx->d_pos, &ctx->d_bcount, &ctx->d_status,
-                      &ctx->d_plain_acc};
+    for (Lane *L : ctx->lanes) {
+        cudaStreamSynchronize(L->stream);
+        free_lane(ctx, L);
+    }
+    ctx->lanes.clear();
+    DevBuf *bufs[] = {&ctx->d_series_ptr, &ctx->d_series_len, &ctx->d_table, &ctx->d_slot,
+                      &ctx->d_pos, &ctx->d_bcount, &ctx->d_status, &ctx->d_plain_acc,
+                      &ctx->d_dev_items, &ctx->d_dev_queue, &ctx->d_dev_table};
     for (DevBuf *b : bufs) dev_release(ctx, *b);
-    if (ctx->h_items.p) cudaFreeHost(ctx->h_items.p);
-    if (ctx->h_table.p) cudaFreeHost(ctx->h_table.p);
-    cudaFree(ctx->d_psi_fx);
-    cudaFree(ctx->d_log_fx);
-    cudaEventDestroy(ctx->ev_start);
-    cudaEventDestroy(ctx->ev_stop);
+    if (ctx->ev_ref) cudaEventDestroy(ctx->ev_ref);
+    if (ctx->d_psi_fx) cudaFree(ctx->d_psi_fx);
+    if (ctx->d_log_fx) cudaFree(ctx->d_log_fx);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return ISYCOS_OK;
@@ -487,7 +551,7 @@ isycos_status isycos_mi_windows(isycos_ctx *ctx, const isycos_window *windows, i
     std::vector<HostWindow> hw;
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
-    return engine_eval(ctx, hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
+    return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
                        pick_stream(ctx, cuda_stream));
 }
 
@@ -502,7 +566,8 @@ isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *win
     std::vector<HostWindow> hw;
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
-    return engine_eval(ctx, hw.data(), n_w, k, out, nx, ny, c, pick_stream(ctx, cuda_stream));
+    return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nx, ny, c,
+                       pick_stream(ctx, cuda_stream));
 }
 
 isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_windows,
@@ -523,12 +588,12 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     const int nt = batched_threads(max_m);
     const size_t smem = batched_smem(max_m, nt);
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_items, sizeof(WorkItem) * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_dev_items, sizeof(WorkItem) * n_w))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_slot, 4 * n_w))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_pos, 4 * n_w))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_bcount, 4 * kBuckets + 64))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_table, sizeof(BucketTable)))) return rc;
-    if ((rc = dev_reserve(ctx, ctx->d_queue, 256))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_dev_table, sizeof(BucketTable)))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_dev_queue, 256))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_status, 256))) return rc;
     PrepArgs pa;
     pa.windows = d_windows;
@@ -539,15 +604,15 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     pa.series_len = reinterpret_cast<const int64_t *>(ctx->d_series_len.p);
     pa.n_series = (int32_t)ctx->series_ptr.size();
     pa.nt = nt;
-    pa.items = reinterpret_cast<WorkItem *>(ctx->d_items.p);
+    pa.items = reinterpret_cast<WorkItem *>(ctx->d_dev_items.p);
     pa.bucket_count = reinterpret_cast<int32_t *>(ctx->d_bcount.p);
     pa.slot_of = reinterpret_cast<int32_t *>(ctx->d_slot.p);
     pa.pos_of = reinterpret_cast<int32_t *>(ctx->d_pos.p);
-    pa.table = reinterpret_cast<BucketTable *>(ctx->d_table.p);
+    pa.table = reinterpret_cast<BucketTable *>(ctx->d_dev_table.p);
     pa.status = reinterpret_cast<int32_t *>(ctx->d_status.p);
     pa.out = d_out;
     cudaError_t e = cudaMemsetAsync(ctx->d_bcount.p, 0, 4 * kBuckets, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_dev_queue.p, 0, 4, st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_prep(pa, st, &launches);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "window preparation");
@@ -556,7 +621,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     BatchArgs a;
     a.items = pa.items;
     a.table = pa.table;
-    a.queue = reinterpret_cast<int32_t *>(ctx->d_queue.p);
+    a.queue = reinterpret_cast<int32_t *>(ctx->d_dev_queue.p);
     a.psi_fx = ctx->d_psi_fx;
     a.log_fx = ctx->d_log_fx;
     a.out = d_out;
@@ -598,7 +663,7 @@ isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *wind
     if (rc) return rc;
     if (n_w == 0) return ISYCOS_OK;
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    if ((rc = dev_reserve(ctx, ctx->d_out, sizeof(isycos_mi_out) * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->lanes[0]->d_out, sizeof(isycos_mi_out) * n_w))) return rc;
     if (!ctx->d_plain_acc.p) {
         if ((rc = dev_reserve(ctx, ctx->d_plain_acc, 256))) return rc;
         cudaError_t e = cudaMemset(ctx->d_plain_acc.p, 0, 256);
@@ -606,7 +671,7 @@ isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *wind
     }
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ctx->d_plain_acc.p);
     int32_t *done = reinterpret_cast<int32_t *>(acc + 2);
-    isycos_mi_out *d_out = reinterpret_cast<isycos_mi_out *>(ctx->d_out.p);
+    isycos_mi_out *d_out = reinterpret_cast<isycos_mi_out *>(ctx->lanes[0]->d_out.p);
     int launches = 0;
     int64_t pairs = 0;
     for (int64_t i = 0; i < n_w; ++i) {
@@ -632,6 +697,21 @@ isycos_status isycos_get_stats(isycos_ctx *ctx, isycos_stats *out) {
     if (!ctx || !out) return ISYCOS_E_INVAL;
     std::lock_guard<std::mutex> g(ctx->stats_mu);
     *out = ctx->stats;
+    // union of the MI kernel intervals
+    std::vector<std::pair<float, float>> iv = ctx->kernel_iv;
+    std::sort(iv.begin(), iv.end());
+    double busy = 0.0, lo = 0.0, hi = -1.0;
+    for (const auto &p : iv) {
+        if (p.first > hi) {
+            if (hi > lo) busy += hi - lo;
+            lo = p.first;
+            hi = p.second;
+        } else if (p.second > hi) {
+            hi = p.second;
+        }
+    }
+    if (hi > lo) busy += hi - lo;
+    out->mi_kernel_ms = busy;
     return ISYCOS_OK;
 }
 
@@ -639,6 +719,7 @@ isycos_status isycos_reset_stats(isycos_ctx *ctx) {
     if (!ctx) return ISYCOS_E_INVAL;
     std::lock_guard<std::mutex> g(ctx->stats_mu);
     memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->kernel_iv.clear();
     return ISYCOS_OK;
 }
 

@@ -8,6 +8,8 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <unordered_map>
 #include <vector>
 
 #include "isycos.h"
@@ -27,6 +29,18 @@ struct DevBuf {
 struct HostBuf {
     void *p = nullptr;
     size_t cap = 0;
+};
+
+// An independent engine lane: a stream with its own work buffers, so that several host
+// threads can drive batches at once (one lane per thread).
+struct Lane {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevBuf d_items, d_queue, d_out, d_nx, d_ny, d_c;
+    DevBuf d_chain_desc, d_chain_steps, d_chain_state, d_chain_recomp, d_chain_out;
+    HostBuf h_items, h_table;          // pinned staging: table + items; results
+    std::vector<int32_t> h_slot;       // per-call bucket slots (reused)
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
 };
 
 // One window of a resident pair as the engine sees it (already validated).
@@ -57,16 +71,21 @@ struct isycos_ctx {
     isy::DevBuf d_series_ptr, d_series_len;
     bool series_dirty = true;
 
-    // Engine work buffers (guarded by engine_mu).
+    // Engine state (guarded by engine_mu; lanes other than 0 are driven by helper threads
+    // while the calling thread holds engine_mu).
     std::mutex engine_mu;
-    isy::DevBuf d_items, d_table, d_queue, d_out, d_nx, d_ny, d_c;
-    isy::DevBuf d_slot, d_pos, d_bcount, d_status, d_plain_acc;
-    isy::HostBuf h_items, h_table;
+    std::vector<isy::Lane *> lanes;      // lane 0 uses `stream`
+    int max_lanes = 8;
+    isy::DevBuf d_table, d_slot, d_pos, d_bcount, d_status, d_plain_acc;
+    isy::DevBuf d_dev_items, d_dev_queue, d_dev_table;   // asynchronous device-array path
+    std::mutex launch_mu;                 // occupancy cache and function attributes
+    std::unordered_map<uint64_t, int> occupancy;   // CTAs per SM by (k, threads, smem)
     size_t smem_set[2] = {0, 0};   // dynamic smem attribute set per (nt = 256, 1024), all k
 
-    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // MI kernel timing
     isycos_stats stats{};
     std::mutex stats_mu;
+    cudaEvent_t ev_ref = nullptr;                        // origin of the kernel intervals
+    std::vector<std::pair<float, float>> kernel_iv;      // MI kernel [start, stop] in ms
 
     // Options.
     int opt_kernel = 0;
@@ -91,16 +110,33 @@ isycos_status host_reserve(isycos_ctx *ctx, HostBuf &b, size_t bytes);
 // Validation of a window against the resident series (host side).
 isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k);
 
-// Evaluate n windows (validated) on `st`, synchronously; results in input order into the
-// host array `out`.  Per-point arrays (host) are optional.  Caller holds engine_mu.
-isycos_status engine_eval(isycos_ctx *ctx, const HostWindow *w, int64_t n, int k,
+// Evaluate n windows (validated) with lane L's buffers on stream st, synchronously; results
+// in input order into the host array `out`.  Per-point arrays (host) are optional.
+isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                           isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
                           cudaStream_t st);
+
+// Lane i of the context (created on first use; lane 0 runs on ctx->stream).
+isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out);
 
 void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches,
                int64_t batches, int64_t incr_windows);
 
 cudaStream_t pick_stream(isycos_ctx *ctx, void *s);
+
+// A window sequence of one pair for the incremental kernel: result i goes to out[out_idx[i]]
+// (out_idx < 0: evaluated for its state only, result dropped).
+struct ChainSpec {
+    int32_t xs = 0, ys = 0;
+    std::vector<int64_t> starts;
+    std::vector<int32_t> sizes;
+    std::vector<int64_t> out_idx;
+};
+
+// Incremental evaluation of chains (chain.cu), one CTA per chain segment, synchronous;
+// results into the host array out of n_out entries.  Caller holds engine_mu.
+isycos_status engine_eval_chains(isycos_ctx *ctx, Lane &L, const ChainSpec *specs, size_t n_specs,
+                                 int k, isycos_mi_out *out, int64_t n_out, cudaStream_t st);
 
 // Stop and free the serving thread of a context (serve.cu).
 void serve_shutdown(isycos_ctx *ctx);

@@ -15,6 +15,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
+#include <unordered_map>
 
 #include "search.h"
 
@@ -58,6 +60,7 @@ public:
 
     bool want(std::vector<WinReq> &req) override {
         asked_.clear();
+        next_chain_ = 0;
         for (;;) {
             if (finished_) return false;
             if (!layer_started_) start_layer();
@@ -117,13 +120,15 @@ private:
         layer_started_ = true;
     }
 
-    // Ask for the grid windows of a scan from position t to the partition's end.
+    // Ask for the grid windows of a scan from position t to the partition's end; the grid
+    // windows of one scan form a chain (each is the previous one moved by delta).
     void ask_grid(const Scan &sc) {
         const int64_t d = delta();
         bool shifted = sc.shifted;
+        const int32_t chain = next_chain_++;
         for (int64_t t = sc.t; t + s_w_ - 1 <= sc.b; t += d) {
             Val v;
-            if (!lookup(t, (int32_t)s_w_, &v)) asked_.push_back(WinReq{t, (int32_t)s_w_});
+            if (!lookup(t, (int32_t)s_w_, &v)) asked_.push_back(WinReq{t, (int32_t)s_w_, chain, false});
             if (prm.pruning && shifted) ask_subs(t);
             shifted = true;
         }
@@ -193,6 +198,7 @@ private:
     }
 
     int64_t s_w_ = 0;
+    int32_t next_chain_ = 0;
     bool layer_started_ = false;
     bool finished_ = false;
     std::vector<Scan> scans_;
@@ -212,6 +218,8 @@ class BuMachine : public SearchMachine {
 public:
     bool want(std::vector<WinReq> &req) override {
         asked_.clear();
+        dest_.clear();
+        next_chain_ = 0;
         for (;;) {
             if (finished_) return false;
             if (phase_ == kStart) {
@@ -221,67 +229,163 @@ public:
                 }
                 ws_ = c_;
                 we_ = c_ + prm.s_min - 1;
-                Val v;
-                if (!lookup(ws_, (int32_t)(we_ - ws_ + 1), &v)) {
-                    asked_.push_back(WinReq{ws_, (int32_t)(we_ - ws_ + 1)});
-                    phase_ = kWaitStart;
-                    break;
-                }
-                begin_climb(v);
-                continue;
+                invalidate_rings();
+                // a climb always evaluates ring N_1 of its first window next: ask it now
+                if (!lookup(ws_, (int32_t)(we_ - ws_ + 1), &start_val_))
+                    ask(ws_, we_, kDestStart, -1, false);
+                if (prm.t_max_idle >= 0 && prm.max_steps > 0) ask_ring(1, false, false);
+                phase_ = kWaitStart;
+                if (asked_.empty()) continue;
+                break;
             }
             if (phase_ == kWaitStart) {
-                Val v;
-                lookup(ws_, (int32_t)(we_ - ws_ + 1), &v);
-                begin_climb(v);
+                begin_climb(start_val_);
                 continue;
             }
             if (phase_ == kRing) {
-                build_ring();
-                for (const Cand &cd : ring_) {
-                    Val v;
-                    if (!lookup(cd.ts, (int32_t)(cd.te - cd.ts + 1), &v))
-                        asked_.push_back(WinReq{cd.ts, (int32_t)(cd.te - cd.ts + 1)});
-                }
-                for (int s = 0; s < 2; ++s) {
-                    if (!ext_[s].use) continue;
-                    Val v;
-                    if (!lookup(ext_[s].ts, (int32_t)(ext_[s].te - ext_[s].ts + 1), &v))
-                        asked_.push_back(WinReq{ext_[s].ts, (int32_t)(ext_[s].te - ext_[s].ts + 1)});
-                }
+                // After a rejection the window stays put and the rings N_r .. N_{T+1} are
+                // evaluated until one improves: ask for all of them at once.
+                const int r = t_idle_ + 1;
+                const int r_last = t_idle_ >= 1 ? prm.t_max_idle + 1 : r;
+                for (int rr = r; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1]);
                 phase_ = kDecide;
-                if (!asked_.empty()) break;
-                continue;
+                break;
             }
             if (phase_ == kDecide) {
-                decide();
+                const int r = t_idle_ + 1;
+                if (!ring_ready(r)) {
+                    phase_ = kRing;
+                    continue;
+                }
+                decide(r);
                 continue;
             }
         }
-        // de-duplicate requests of this round
         req.insert(req.end(), asked_.begin(), asked_.end());
         return true;
     }
 
-    void give(const isycos_mi_out *res, size_t n) override { absorb(res, n); }
+    void give(const isycos_mi_out *res, size_t n) override {
+        absorb(res, n);
+        for (size_t i = 0; i < n && i < dest_.size(); ++i) {
+            const Dest &d = dest_[i];
+            const Val v{score_of(res[i]), res[i].mi};
+            if (d.kind == kDestStart) {
+                start_val_ = v;
+            } else if (d.kind == kDestCell) {
+                rings_[d.r].val[d.idx] = v;
+                rings_[d.r].have[d.idx] = 1;
+            } else if (d.kind == kDestExt) {
+                rings_[d.r].ext_val[d.idx] = v;
+                rings_[d.r].ext_have[d.idx] = 1;
+            }
+        }
+    }
 
     void init() {
         c_ = t_begin;
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
+        rings_.resize((size_t)prm.t_max_idle + 2);
     }
 
 private:
     enum Phase { kStart, kWaitStart, kRing, kDecide };
-    struct Cand {
-        int64_t ts, te;
-        int a, b;
+    enum DestKind { kDestStart, kDestCell, kDestExt, kDestNone };
+    struct Dest {
+        int kind, r, idx;
     };
-    struct Ext {
-        bool use;
-        int64_t ts, te;
-        bool pure_found;   // the pure extension neighbour is part of the ring
+    // Results for ring N_r around the centre (cs, ce): a cell per offset (a, b).
+    struct Ring {
+        bool asked = false;
+        int64_t cs = 0, ce = -1;
+        std::vector<Val> val;
+        std::vector<char> have;
+        Val ext_val[2];
+        char ext_have[2] = {0, 0};
     };
+
+    void ask(int64_t ts, int64_t te, int kind, int r, bool base, int idx = 0, int32_t chain = -1) {
+        asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), chain, base});
+        dest_.push_back(Dest{base ? (int)kDestNone : kind, r, idx});
+    }
+
+    void invalidate_rings() {
+        for (Ring &g : rings_) g.asked = false;
+    }
+
+    bool ring_ready(int r) const {
+        const Ring &g = rings_[r];
+        return g.asked && g.cs == ws_ && g.ce == we_;
+    }
+
+    // A candidate of ring N_r around (ws_, we_) passes the filters of the search.
+    bool keep(int64_t a, int64_t b, int64_t r, bool drop_left, bool drop_right, int64_t *ts,
+              int64_t *te) const {
+        if (std::max(a < 0 ? -a : a, b < 0 ? -b : b) != r) return false;
+        if (drop_left && a < 0) return false;
+        if (drop_right && b > 0) return false;
+        const int64_t d = prm.delta_bu;
+        *ts = ws_ + a * d;
+        *te = we_ + b * d;
+        const int64_t mm = *te - *ts + 1;
+        if (mm < prm.s_min || mm > prm.s_max) return false;
+        if (*ts < t_begin || *te > t_end - 1 || *ts <= last_end_) return false;
+        return true;
+    }
+
+    // Ask for ring N_r around the current window: the candidates walked along the perimeter
+    // from (-r, -r) so that consecutive windows differ by one delta at one end (the current
+    // window starts the chain), then the noise-test extension windows.
+    void ask_ring(int r, bool drop_left, bool drop_right) {
+        Ring &g = rings_[r];
+        const int side = 2 * r + 1;
+        g.asked = true;
+        g.cs = ws_;
+        g.ce = we_;
+        g.val.assign((size_t)side * side, Val{0.0, 0.0});
+        g.have.assign((size_t)side * side, 0);
+        g.ext_have[0] = g.ext_have[1] = 0;
+        const int32_t chain = next_chain_++;
+        const size_t first = asked_.size();
+        auto visit = [&](int a, int b) {
+            int64_t ts, te;
+            if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
+            const int idx = (a + r) * side + (b + r);
+            Val v;
+            if (lookup(ts, (int32_t)(te - ts + 1), &v)) {   // evaluated earlier in this climb
+                g.val[idx] = v;
+                g.have[idx] = 1;
+                return;
+            }
+            ask(ts, te, kDestCell, r, false, idx, chain);
+        };
+        for (int b = -r; b <= r; ++b) visit(-r, b);
+        for (int a = -r + 1; a <= r; ++a) visit(a, r);
+        for (int b = r - 1; b >= -r; --b) visit(r, b);
+        for (int a = r - 1; a > -r; --a) visit(a, -r);
+        if (asked_.size() > first + 1) {
+            asked_.insert(asked_.begin() + first, WinReq{ws_, (int32_t)(we_ - ws_ + 1), chain, true});
+            dest_.insert(dest_.begin() + first, Dest{kDestNone, r, 0});
+        } else if (asked_.size() == first + 1) {
+            asked_.back().chain = -1;
+        }
+        if (prm.pruning && (int64_t)r * prm.delta_bu >= prm.k + 1) {
+            int64_t ts, te;
+            const int64_t span = (int64_t)r * prm.delta_bu;
+            const int64_t es[2] = {ws_ - span, we_ + 1}, ee[2] = {ws_ - 1, we_ + span};
+            for (int sd = 0; sd < 2; ++sd) {
+                if (!keep(sd == 0 ? -r : 0, sd == 0 ? 0 : r, r, drop_left, drop_right, &ts, &te)) continue;
+                Val v;
+                if (lookup(es[sd], (int32_t)(ee[sd] - es[sd] + 1), &v)) {
+                    g.ext_val[sd] = v;
+                    g.ext_have[sd] = 1;
+                } else {
+                    ask(es[sd], ee[sd], kDestExt, r, false, sd);
+                }
+            }
+        }
+    }
 
     void begin_climb(const Val &v) {
         Iw_ = v.score;
@@ -293,67 +397,53 @@ private:
         run_[0] = run_[1] = 0;
         dropped_[0] = dropped_[1] = false;
         if (t_idle_ <= prm.t_max_idle && step_ < (uint64_t)prm.max_steps)
-            phase_ = kRing;
+            phase_ = kDecide;   // ring N_1 was asked together with the start window
         else
             end_climb();
     }
 
-    void build_ring() {
-        ring_.clear();
-        const int64_t r = t_idle_ + 1, d = prm.delta_bu;
-        ext_[0] = Ext{false, 0, 0, false};
-        ext_[1] = Ext{false, 0, 0, false};
-        for (int64_t a = -r; a <= r; ++a)
-            for (int64_t b = -r; b <= r; ++b) {
-                if (std::max(a < 0 ? -a : a, b < 0 ? -b : b) != r) continue;
-                if (dropped_[0] && a < 0) continue;
-                if (dropped_[1] && b > 0) continue;
-                const int64_t ts = ws_ + a * d, te = we_ + b * d, mm = te - ts + 1;
-                if (mm < prm.s_min || mm > prm.s_max) continue;
-                if (ts < t_begin || te > t_end - 1 || ts <= last_end_) continue;
-                ring_.push_back(Cand{ts, te, (int)a, (int)b});
-                if (prm.pruning && a == -r && b == 0) ext_[0].pure_found = true;
-                if (prm.pruning && a == 0 && b == r) ext_[1].pure_found = true;
-            }
-        if (prm.pruning) {
-            if (ext_[0].pure_found && r * d >= prm.k + 1) {
-                ext_[0].use = true;
-                ext_[0].ts = ws_ - r * d;
-                ext_[0].te = ws_ - 1;
-            }
-            if (ext_[1].pure_found && r * d >= prm.k + 1) {
-                ext_[1].use = true;
-                ext_[1].ts = we_ + 1;
-                ext_[1].te = we_ + r * d;
-            }
-        }
-    }
-
-    void decide() {
-        const int64_t r = t_idle_ + 1;
+    // One LAHC step on ring N_r (Algorithm 2), with the current dropped directions.
+    void decide(int r) {
+        const Ring &g = rings_[r];
+        const int side = 2 * r + 1;
         bool have = false;
-        Cand best{};
+        int64_t bs = 0, be = 0;
         Val bv{0.0, 0.0};
         double pure_sc[2] = {0.0, 0.0};
-        for (const Cand &cd : ring_) {
-            Val v;
-            lookup(cd.ts, (int32_t)(cd.te - cd.ts + 1), &v);
-            ++evals;
-            if (!have || v.score > bv.score) {
-                have = true;
-                best = cd;
-                bv = v;
+        bool pure_found[2] = {false, false};
+        for (int64_t a = -r; a <= r; ++a)
+            for (int64_t b = -r; b <= r; ++b) {
+                int64_t ts, te;
+                if (!keep(a, b, r, dropped_[0], dropped_[1], &ts, &te)) continue;
+                const size_t idx = (size_t)(a + r) * side + (b + r);
+                if (!g.have[idx]) {   // cannot happen: asked with fewer directions dropped
+                    phase_ = kRing;
+                    rings_[r].asked = false;
+                    return;
+                }
+                const Val &v = g.val[idx];
+                ++evals;
+                if (!have || v.score > bv.score) {        // first maximum wins
+                    have = true;
+                    bs = ts;
+                    be = te;
+                    bv = v;
+                }
+                if (a == -r && b == 0) {
+                    pure_found[0] = true;
+                    pure_sc[0] = v.score;
+                }
+                if (a == 0 && b == r) {
+                    pure_found[1] = true;
+                    pure_sc[1] = v.score;
+                }
             }
-            if (cd.a == -r && cd.b == 0) pure_sc[0] = v.score;
-            if (cd.a == 0 && cd.b == r) pure_sc[1] = v.score;
-        }
         if (prm.pruning) {
             for (int s = 0; s < 2; ++s) {
-                if (!ext_[s].pure_found) continue;
+                if (!pure_found[s]) continue;
                 bool noise = false;
-                if (ext_[s].use) {
-                    Val e;
-                    lookup(ext_[s].ts, (int32_t)(ext_[s].te - ext_[s].ts + 1), &e);
+                if ((int64_t)r * prm.delta_bu >= prm.k + 1) {
+                    const Val &e = g.ext_val[s];
                     ++evals;
                     // Def. 6.2 with w = current window, w' = extension, w'' = the neighbour.
                     noise = (Iw_ > 0.0) && (e.score < prm.tau) && (pure_sc[s] < Iw_);
@@ -364,8 +454,8 @@ private:
         }
         const int v = (int)(splitmix64_at(prm.seed, (climb_ << 32) + step_ + 1) % (uint64_t)prm.h);
         if (have && (bv.score > L_[v] || bv.score > Iw_)) {
-            ws_ = best.ts;
-            we_ = best.te;
+            ws_ = bs;
+            we_ = be;
             Iw_ = bv.score;
             mw_ = bv.mi;
             t_idle_ = 0;
@@ -375,7 +465,7 @@ private:
         if (Iw_ > L_[v]) L_[v] = Iw_;
         ++step_;
         if (t_idle_ <= prm.t_max_idle && step_ < (uint64_t)prm.max_steps)
-            phase_ = kRing;
+            phase_ = kDecide;
         else
             end_climb();
     }
@@ -388,7 +478,7 @@ private:
         c_ = std::max(we_ + 1, c_ + prm.s_min);
         ++climb_;
         phase_ = kStart;
-        if (cache_.size() > (1u << 16)) cache_.clear();
+        if (cache_.size() > 4096) cache_.clear();   // O(1): generation bump
     }
 
     void finish() {
@@ -401,13 +491,15 @@ private:
     bool finished_ = false;
     int64_t c_ = 0, last_end_ = -1, ws_ = 0, we_ = 0;
     double Iw_ = 0.0, mw_ = 0.0;
+    Val start_val_{0.0, 0.0};
     std::vector<double> L_;
     int t_idle_ = 0;
     uint64_t step_ = 0, climb_ = 0;
     int run_[2] = {0, 0};
     bool dropped_[2] = {false, false};
-    std::vector<Cand> ring_;
-    Ext ext_[2];
+    std::vector<Ring> rings_;
+    std::vector<Dest> dest_;
+    int32_t next_chain_ = 0;
 };
 
 }  // namespace
@@ -434,70 +526,140 @@ std::unique_ptr<SearchMachine> make_machine(int32_t xs, int32_t ys, int64_t t_be
     return m;
 }
 
-isycos_status step_machines(isycos_ctx *ctx, std::vector<SearchMachine *> &ms,
+namespace {
+
+// Work of a chain in units of pair comparisons: the first window from scratch, then per step
+// the points moved times the window (influence checks, re-searched and added points).
+double chain_cost(const std::vector<const WinReq *> &g, int k) {
+    double c = (double)g[0]->m * g[0]->m;
+    for (size_t i = 1; i < g.size(); ++i) {
+        const int64_t s0 = g[i - 1]->start, e0 = s0 + g[i - 1]->m - 1;
+        const int64_t s1 = g[i]->start, e1 = s1 + g[i]->m - 1;
+        const int64_t inter = std::max<int64_t>(0, std::min(e0, e1) - std::max(s0, s1) + 1);
+        const int64_t moved = (e0 - s0 + 1) + (e1 - s1 + 1) - 2 * inter;
+        c += (double)moved * g[i]->m * (k + 3);
+    }
+    return c;
+}
+
+double scratch_cost(const std::vector<const WinReq *> &g) {
+    double c = 0.0;
+    for (const WinReq *r : g)
+        if (!r->base) c += (double)r->m * r->m;
+    return c;
+}
+
+}  // namespace
+
+isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
                             std::vector<bool> &finished, cudaStream_t st, int64_t *n_eval) {
-    std::vector<HostWindow> batch;
-    std::vector<size_t> first(ms.size(), 0), count(ms.size(), 0);
-    std::vector<WinReq> req;
+    thread_local std::vector<std::vector<WinReq>> reqs;
+    if (reqs.size() < ms.size()) reqs.resize(ms.size());
+    for (size_t q = 0; q < ms.size(); ++q) reqs[q].clear();
+    thread_local std::vector<size_t> first;
+    first.assign(ms.size(), 0);
+    size_t total = 0;
     int k = 0;
+    thread_local std::vector<char> active_tl;
+    std::vector<char> &active = active_tl;
+    std::vector<std::vector<WinReq>> &rq_all = reqs;
+    active.assign(ms.size(), 0);
+    for (size_t q = 0; q < ms.size(); ++q)
+        if (!finished[q]) active[q] = ms[q]->want(rq_all[q]) ? 1 : 0;
     for (size_t q = 0; q < ms.size(); ++q) {
         if (finished[q]) continue;
-        req.clear();
-        if (!ms[q]->want(req)) {
+        if (!active[q]) {
             finished[q] = true;
             continue;
         }
-        k = ms[q]->prm.k;
-        first[q] = batch.size();
-        count[q] = req.size();
-        for (const WinReq &r : req) batch.push_back(HostWindow{ms[q]->xs, ms[q]->ys, r.start, r.m});
+        if (k && ms[q]->prm.k != k) k = -1;
+        if (k == 0) k = ms[q]->prm.k;
+        first[q] = total;
+        total += reqs[q].size();
     }
-    if (n_eval) *n_eval = (int64_t)batch.size();
-    if (batch.empty()) return ISYCOS_OK;
-    // Machines of one call share k (the batch kernel is specialised on k); group otherwise.
-    std::vector<isycos_mi_out> res(batch.size());
-    bool mixed = false;
-    for (size_t q = 0; q < ms.size(); ++q)
-        if (count[q] && ms[q]->prm.k != k) mixed = true;
-    if (!mixed) {
-        isycos_status rc = engine_eval(ctx, batch.data(), (int64_t)batch.size(), k, res.data(),
-                                       nullptr, nullptr, nullptr, st);
-        if (rc) return rc;
-    } else {
-        for (int kk = 1; kk <= kMaxK; ++kk) {
-            std::vector<HostWindow> sub;
-            std::vector<size_t> where;
-            for (size_t q = 0; q < ms.size(); ++q)
-                if (count[q] && ms[q]->prm.k == kk)
-                    for (size_t i = 0; i < count[q]; ++i) {
-                        sub.push_back(batch[first[q] + i]);
-                        where.push_back(first[q] + i);
-                    }
-            if (sub.empty()) continue;
-            std::vector<isycos_mi_out> r2(sub.size());
-            isycos_status rc = engine_eval(ctx, sub.data(), (int64_t)sub.size(), kk, r2.data(),
+    if (n_eval) *n_eval = (int64_t)total;
+    if (total == 0) return ISYCOS_OK;
+    thread_local std::vector<isycos_mi_out> res;
+    res.resize(total);
+    // Per k (machines of one call normally share it), split the requests into the batched
+    // list and the chains that the incremental kernel takes.
+    for (int kk = 1; kk <= kMaxK; ++kk) {
+        if (k > 0 && kk != k) continue;
+        std::vector<HostWindow> batch;
+        std::vector<size_t> where;
+        std::vector<ChainSpec> chains;
+        for (size_t q = 0; q < ms.size(); ++q) {
+            if (finished[q] || reqs[q].empty() || ms[q]->prm.k != kk) continue;
+            const auto &rq = reqs[q];
+            int32_t n_groups = 0;
+            for (const WinReq &r : rq) n_groups = std::max(n_groups, r.chain + 1);
+            thread_local std::vector<char> in_chain;
+            in_chain.assign(rq.size(), 0);
+            if (ctx->opt_incremental == 0) n_groups = 0;
+            thread_local std::vector<std::vector<size_t>> groups;
+            if (groups.size() < (size_t)n_groups) groups.resize((size_t)n_groups);
+            for (int32_t gi = 0; gi < n_groups; ++gi) groups[gi].clear();
+            for (size_t i = 0; i < rq.size(); ++i)
+                if (rq[i].chain >= 0 && rq[i].chain < n_groups) groups[rq[i].chain].push_back(i);
+            for (int32_t gi = 0; gi < n_groups; ++gi) {
+                const std::vector<size_t> &members = groups[gi];
+                if (members.size() < 2) continue;
+                std::vector<const WinReq *> g;
+                for (size_t i : members) g.push_back(&rq[i]);
+                bool use = false;
+                if (g.size() >= 2 && ctx->opt_incremental == 2) use = true;
+                if (g.size() >= 2 && ctx->opt_incremental == 1)
+                    use = chain_cost(g, kk) < 0.5 * scratch_cost(g);
+                if (!use) continue;
+                ChainSpec sp;
+                sp.xs = ms[q]->xs;
+                sp.ys = ms[q]->ys;
+                for (size_t i : members) {
+                    sp.starts.push_back(rq[i].start);
+                    sp.sizes.push_back(rq[i].m);
+                    sp.out_idx.push_back(rq[i].base ? -1 : (int64_t)(first[q] + i));
+                    in_chain[i] = 1;
+                }
+                chains.push_back(std::move(sp));
+            }
+            for (size_t i = 0; i < rq.size(); ++i) {
+                if (in_chain[i] || rq[i].base) continue;
+                batch.push_back(HostWindow{ms[q]->xs, ms[q]->ys, rq[i].start, rq[i].m});
+                where.push_back(first[q] + i);
+            }
+        }
+        if (!batch.empty()) {
+            std::vector<isycos_mi_out> r2(batch.size());
+            isycos_status rc = engine_eval(ctx, L, batch.data(), (int64_t)batch.size(), kk, r2.data(),
                                            nullptr, nullptr, nullptr, st);
             if (rc) return rc;
-            for (size_t i = 0; i < sub.size(); ++i) res[where[i]] = r2[i];
+            for (size_t i = 0; i < batch.size(); ++i) res[where[i]] = r2[i];
+        }
+        if (!chains.empty()) {
+            isycos_status rc = engine_eval_chains(ctx, L, chains.data(), chains.size(), kk, res.data(),
+                                                  (int64_t)total, st);
+            if (rc) return rc;
         }
     }
+    std::vector<isycos_mi_out> &res_all = res;
+    std::vector<size_t> &first_all = first;
     for (size_t q = 0; q < ms.size(); ++q)
-        if (count[q]) ms[q]->give(res.data() + first[q], count[q]);
+        if (!finished[q] && !rq_all[q].empty()) ms[q]->give(res_all.data() + first_all[q], rq_all[q].size());
     return ISYCOS_OK;
 }
 
-isycos_status run_machines(isycos_ctx *ctx, std::vector<SearchMachine *> &ms, cudaStream_t st) {
+isycos_status run_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
+                           cudaStream_t st) {
     std::vector<bool> finished(ms.size(), false);
     for (;;) {
         int64_t n = 0;
-        isycos_status rc = step_machines(ctx, ms, finished, st, &n);
+        isycos_status rc = step_machines(ctx, L, ms, finished, st, &n);
         if (rc) return rc;
         bool all = true;
         for (bool f : finished) all = all && f;
         if (all) return ISYCOS_OK;
     }
 }
-
 }  // namespace isy
 
 using namespace isy;
@@ -543,7 +705,27 @@ isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
         own.push_back(make_machine(xs[q], ys[q], t_begin[q], t_end[q], p));
         ms.push_back(own.back().get());
     }
-    if ((rc = run_machines(ctx, ms, ctx->stream))) return rc;
+    // Independent queries split over engine lanes, one host thread per lane: each thread runs
+    // its machines' rounds on its own stream, so that the sequential decision logic of many
+    // queries proceeds in parallel and their small batches overlap on the GPU.
+    const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 7) / 8));
+    std::vector<Lane *> lanes((size_t)n_lanes);
+    for (int i = 0; i < n_lanes; ++i)
+        if ((rc = get_lane(ctx, i, &lanes[i]))) return rc;
+    std::vector<std::vector<SearchMachine *>> parts((size_t)n_lanes);
+    for (size_t q = 0; q < ms.size(); ++q) parts[q % n_lanes].push_back(ms[q]);
+    std::vector<isycos_status> st((size_t)n_lanes, ISYCOS_OK);
+    std::vector<std::thread> th;
+    const int dev = ctx->device;
+    for (int i = 1; i < n_lanes; ++i)
+        th.emplace_back([&, i] {
+            cudaSetDevice(dev);
+            st[i] = run_machines(ctx, *lanes[i], parts[i], lanes[i]->stream);
+        });
+    st[0] = run_machines(ctx, *lanes[0], parts[0], lanes[0]->stream);
+    for (auto &t : th) t.join();
+    for (isycos_status s1 : st)
+        if (s1) return s1;
     isycos_status result = ISYCOS_OK;
     for (int64_t q = 0; q < n_q; ++q) {
         const auto &f = ms[q]->found;

@@ -5,7 +5,6 @@
 #include <stdint.h>
 
 #include <memory>
-#include <unordered_map>
 #include <vector>
 
 #include "runtime.h"
@@ -30,6 +29,8 @@ isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchPar
 struct WinReq {
     int64_t start;
     int32_t m;
+    int32_t chain = -1;   // >= 0: consecutive requests with this id form one chain (in order)
+    bool base = false;    // the chain's first window, asked only as the chain's start state
 };
 
 class SearchMachine {
@@ -48,21 +49,82 @@ public:
 
 protected:
     double score_of(const isycos_mi_out &r) const { return prm.score_kind == 1 ? r.mi : r.nmi; }
-    static uint64_t key(int64_t start, int32_t m) { return ((uint64_t)start << 15) ^ (uint64_t)m; }
+    static uint64_t key(int64_t start, int32_t m) { return ((uint64_t)start << 15) | (uint64_t)m; }
     struct Val {
         double score, mi;
     };
-    std::unordered_map<uint64_t, Val> cache_;
+    // Scores of windows already evaluated: open addressing with linear probing, cleared in
+    // O(1) by a generation counter (no allocation per insert).
+    class FlatCache {
+    public:
+        bool find(uint64_t k, Val *v) const {
+            if (slots_.empty()) return false;
+            for (size_t i = hash(k) & mask_;; i = (i + 1) & mask_) {
+                const Slot &s = slots_[i];
+                if (s.gen != gen_) return false;
+                if (s.key == k) {
+                    *v = s.val;
+                    return true;
+                }
+            }
+        }
+        void put(uint64_t k, const Val &v) {
+            if ((used_ + 1) * 2 > slots_.size()) grow();
+            for (size_t i = hash(k) & mask_;; i = (i + 1) & mask_) {
+                Slot &s = slots_[i];
+                if (s.gen != gen_) {
+                    s.gen = gen_;
+                    s.key = k;
+                    s.val = v;
+                    ++used_;
+                    return;
+                }
+                if (s.key == k) {
+                    s.val = v;
+                    return;
+                }
+            }
+        }
+        void clear() {
+            ++gen_;
+            used_ = 0;
+        }
+        size_t size() const { return used_; }
+
+    private:
+        struct Slot {
+            uint64_t key;
+            uint32_t gen;
+            Val val;
+        };
+        static size_t hash(uint64_t k) {
+            k ^= k >> 33;
+            k *= 0xff51afd7ed558ccdULL;
+            k ^= k >> 33;
+            return (size_t)k;
+        }
+        void grow() {
+            std::vector<Slot> old;
+            old.swap(slots_);
+            const size_t cap = old.empty() ? 1024 : old.size() * 2;
+            slots_.assign(cap, Slot{0, 0, Val{0.0, 0.0}});
+            mask_ = cap - 1;
+            const uint32_t g = gen_;
+            gen_ = 1;
+            used_ = 0;
+            for (const Slot &s : old)
+                if (s.gen == g) put(s.key, s.val);
+        }
+        std::vector<Slot> slots_;
+        size_t mask_ = 0, used_ = 0;
+        uint32_t gen_ = 1;
+    };
+    FlatCache cache_;
     std::vector<WinReq> asked_;
-    bool lookup(int64_t start, int32_t m, Val *v) const {
-        auto it = cache_.find(key(start, m));
-        if (it == cache_.end()) return false;
-        *v = it->second;
-        return true;
-    }
+    bool lookup(int64_t start, int32_t m, Val *v) const { return cache_.find(key(start, m), v); }
     void absorb(const isycos_mi_out *res, size_t n) {
         for (size_t i = 0; i < n && i < asked_.size(); ++i)
-            cache_[key(asked_[i].start, asked_[i].m)] = Val{score_of(res[i]), res[i].mi};
+            if (!asked_[i].base) cache_.put(key(asked_[i].start, asked_[i].m), Val{score_of(res[i]), res[i].mi});
     }
 };
 
@@ -71,11 +133,12 @@ std::unique_ptr<SearchMachine> make_machine(int32_t xs, int32_t ys, int64_t t_be
 
 // Drive machines to completion, merging their requests into common GPU batches.
 // Caller holds ctx->engine_mu.
-isycos_status run_machines(isycos_ctx *ctx, std::vector<SearchMachine *> &ms, cudaStream_t st);
+isycos_status run_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
+                           cudaStream_t st);
 
 // One round for the serving loop: collect requests, evaluate them in one batch, deliver.
 // Returns the number of windows evaluated.  Caller holds ctx->engine_mu.
-isycos_status step_machines(isycos_ctx *ctx, std::vector<SearchMachine *> &ms,
+isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
                             std::vector<bool> &finished, cudaStream_t st, int64_t *n_eval);
 
 }  // namespace isy

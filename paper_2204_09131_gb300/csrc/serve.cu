@@ -204,7 +204,7 @@ private:
                 std::lock_guard<std::mutex> eg(ctx_->engine_mu);
                 cudaSetDevice(ctx_->device);
                 int64_t n = 0;
-                rc = step_machines(ctx_, ms, finished, ctx_->stream, &n);
+                rc = step_machines(ctx_, *ctx_->lanes[0], ms, finished, ctx_->stream, &n);
             }
             std::lock_guard<std::mutex> g(mu_);
             for (size_t i = 0; i < batch.size(); ++i) {

@@ -226,3 +226,34 @@ def test_serving_admission_under_a_small_budget():
         assert all(np.array_equal(r[0], ref) for r in res)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("opt", [0, 1, 2])
+@pytest.mark.parametrize("extra", [dict(mode=0, delta_td=4, s_min=48, s_max=192, pruning=1),
+                                   dict(mode=1, pruning=1, seed=3),
+                                   dict(mode=1, pruning=0, s_max=1024, seed=8)],
+                         ids=["td-small-delta", "bu-pruning", "bu-large"])
+def test_search_with_incremental_updates(ctx, opt, extra):
+    """Searches whose frontiers run through the incremental kernel (opt 2: every chain;
+    opt 1: chains the cost model picks; opt 0: none) give the oracle's windows."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, seed=11)
+    kw.update(extra)
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    api.isycos_set_option(ctx, api.OPT_INCREMENTAL, opt)
+    api.isycos_reset_stats(ctx)
+    try:
+        got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_INCREMENTAL, 1)
+    st = api.isycos_get_stats(ctx)
+    if opt == 2:
+        assert st["incr_windows"] > 0
+    if opt == 0:
+        assert st["incr_windows"] == 0
+    okw = dict(kw)
+    mode = okw.pop("mode")
+    ref, _ = (O.search_td if mode == 0 else O.search_bu)(x, y, **okw)
+    _same(got, ref)
