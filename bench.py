@@ -61,11 +61,13 @@ def dist_env():
     return rank, world, local
 
 
-def make_pairs(rank, n_pairs, length):
-    from paper_2204_09131_gb300 import synth
+def make_pairs(rank, n_pairs, length, world=1):
+    """This rank's pairs: every world-th of world * n_pairs pairs (weak scaling, no collective
+    on the data path)."""
+    from paper_2204_09131_gb300 import shard, synth
     pairs = []
-    for p in range(n_pairs):
-        x, y, _ = synth.planted_pair(2, rank * n_pairs + p, length)
+    for p in shard.shard_indices(world * n_pairs, rank, world):
+        x, y, _ = synth.planted_pair(2, p, length)
         pairs.append((x, y))
     return pairs
 
@@ -341,7 +343,7 @@ def main():
         dist.barrier()
     from paper_2204_09131_gb300 import api
 
-    pairs = make_pairs(rank, args.pairs, args.length)
+    pairs = make_pairs(rank, args.pairs, args.length, world)
     ctx = api.isycos_create(local, 0)
     ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
     l2buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

@@ -230,10 +230,13 @@ public:
                 ws_ = c_;
                 we_ = c_ + prm.s_min - 1;
                 invalidate_rings();
+                grid_.reset(ws_, we_, prm.delta_bu);
                 // a climb always evaluates ring N_1 of its first window next: ask it now
                 if (!lookup(ws_, (int32_t)(we_ - ws_ + 1), &start_val_))
                     ask(ws_, we_, kDestStart, -1, false);
-                if (prm.t_max_idle >= 0 && prm.max_steps > 0) ask_ring(1, false, false);
+                if (prm.t_max_idle >= 0 && prm.max_steps > 0)
+                    for (int rr = 1; rr <= std::min(prm.t_max_idle + 1, spec_depth()); ++rr)
+                        ask_ring(rr, false, false);
                 phase_ = kWaitStart;
                 if (asked_.empty()) continue;
                 break;
@@ -246,9 +249,18 @@ public:
                 // After a rejection the window stays put and the rings N_r .. N_{T+1} are
                 // evaluated until one improves: ask for all of them at once.
                 const int r = t_idle_ + 1;
-                const int r_last = t_idle_ >= 1 ? prm.t_max_idle + 1 : r;
-                for (int rr = r; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1]);
+                int r_last = t_idle_ >= 1 ? prm.t_max_idle + 1 : r;
+                // Small windows are cheap on the GPU and every round trip costs the same: also
+                // ask the outer rings now, which cover the next step's ring N_1 when the
+                // climb moves by one delta and the remaining rings when it does not.
+                r_last = std::max(r_last, std::min(prm.t_max_idle + 1, spec_depth()));
+                const size_t before = asked_.size();
+                ask_ring(r, dropped_[0], dropped_[1]);
+                // speculate only when this step needs a round trip anyway
+                if (asked_.size() > before)
+                    for (int rr = r + 1; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1]);
                 phase_ = kDecide;
+                if (asked_.empty()) continue;
                 break;
             }
             if (phase_ == kDecide) {
@@ -266,18 +278,20 @@ public:
     }
 
     void give(const isycos_mi_out *res, size_t n) override {
-        absorb(res, n);
         for (size_t i = 0; i < n && i < dest_.size(); ++i) {
             const Dest &d = dest_[i];
             const Val v{score_of(res[i]), res[i].mi};
             if (d.kind == kDestStart) {
                 start_val_ = v;
+                cache_.put(key(d.ts, (int32_t)(d.te - d.ts + 1)), v);
             } else if (d.kind == kDestCell) {
                 rings_[d.r].val[d.idx] = v;
                 rings_[d.r].have[d.idx] = 1;
+                grid_.put(d.ts, d.te, v);
             } else if (d.kind == kDestExt) {
                 rings_[d.r].ext_val[d.idx] = v;
                 rings_[d.r].ext_have[d.idx] = 1;
+                cache_.put(key(d.ts, (int32_t)(d.te - d.ts + 1)), v);
             }
         }
     }
@@ -294,6 +308,65 @@ private:
     enum DestKind { kDestStart, kDestCell, kDestExt, kDestNone };
     struct Dest {
         int kind, r, idx;
+        int64_t ts, te;
+    };
+    // Scores of this climb's windows on its delta grid: window [c + a d, c + s_min - 1 + b d]
+    // at cell (a, b) of a square array that follows the current window.
+    struct GridCache {
+        static constexpr int G = 64;
+        int64_t bs = 0, be = 0, d = 1;
+        int64_t a0 = 0, b0 = 0;   // offsets of cell (0, 0)
+        uint32_t gen = 1;
+        std::vector<Val> val = std::vector<Val>((size_t)G * G);
+        std::vector<uint32_t> tag = std::vector<uint32_t>((size_t)G * G, 0);
+        void reset(int64_t s, int64_t e, int64_t delta) {
+            bs = s;
+            be = e;
+            d = delta;
+            a0 = b0 = -G / 2;
+            ++gen;
+        }
+        bool cell(int64_t ts, int64_t te, size_t *idx) const {
+            const int64_t da = ts - bs, db = te - be;
+            if (da % d != 0 || db % d != 0) return false;
+            const int64_t a = da / d - a0, b = db / d - b0;
+            if (a < 0 || a >= G || b < 0 || b >= G) return false;
+            *idx = (size_t)a * G + (size_t)b;
+            return true;
+        }
+        bool get(int64_t ts, int64_t te, Val *v) const {
+            size_t i;
+            if (!cell(ts, te, &i) || tag[i] != gen) return false;
+            *v = val[i];
+            return true;
+        }
+        void put(int64_t ts, int64_t te, const Val &v) {
+            size_t i;
+            if (!cell(ts, te, &i)) return;
+            val[i] = v;
+            tag[i] = gen;
+        }
+        // keep the square of half-side R around the window (ws, we) inside the array
+        void follow(int64_t ws, int64_t we, int R) {
+            const int64_t ac = (ws - bs) / d, bc = (we - be) / d;
+            if (ac - R >= a0 && ac + R < a0 + G && bc - R >= b0 && bc + R < b0 + G) return;
+            std::vector<Val> nv((size_t)G * G);
+            std::vector<uint32_t> nt((size_t)G * G, 0);
+            const int64_t na0 = ac - G / 2, nb0 = bc - G / 2;
+            for (int64_t a = 0; a < G; ++a)
+                for (int64_t b = 0; b < G; ++b) {
+                    const size_t i = (size_t)a * G + (size_t)b;
+                    if (tag[i] != gen) continue;
+                    const int64_t ga = a + a0 - na0, gb = b + b0 - nb0;
+                    if (ga < 0 || ga >= G || gb < 0 || gb >= G) continue;
+                    nv[(size_t)ga * G + (size_t)gb] = val[i];
+                    nt[(size_t)ga * G + (size_t)gb] = gen;
+                }
+            val.swap(nv);
+            tag.swap(nt);
+            a0 = na0;
+            b0 = nb0;
+        }
     };
     // Results for ring N_r around the centre (cs, ce): a cell per offset (a, b).
     struct Ring {
@@ -307,7 +380,7 @@ private:
 
     void ask(int64_t ts, int64_t te, int kind, int r, bool base, int idx = 0, int32_t chain = -1) {
         asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), chain, base});
-        dest_.push_back(Dest{base ? (int)kDestNone : kind, r, idx});
+        dest_.push_back(Dest{base ? (int)kDestNone : kind, r, idx, ts, te});
     }
 
     void invalidate_rings() {
@@ -338,6 +411,7 @@ private:
     // from (-r, -r) so that consecutive windows differ by one delta at one end (the current
     // window starts the chain), then the noise-test extension windows.
     void ask_ring(int r, bool drop_left, bool drop_right) {
+        grid_.follow(ws_, we_, r + 1);
         Ring &g = rings_[r];
         const int side = 2 * r + 1;
         g.asked = true;
@@ -353,7 +427,7 @@ private:
             if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
             const int idx = (a + r) * side + (b + r);
             Val v;
-            if (lookup(ts, (int32_t)(te - ts + 1), &v)) {   // evaluated earlier in this climb
+            if (grid_.get(ts, te, &v)) {   // evaluated earlier in this climb
                 g.val[idx] = v;
                 g.have[idx] = 1;
                 return;
@@ -366,7 +440,7 @@ private:
         for (int a = r - 1; a > -r; --a) visit(a, -r);
         if (asked_.size() > first + 1) {
             asked_.insert(asked_.begin() + first, WinReq{ws_, (int32_t)(we_ - ws_ + 1), chain, true});
-            dest_.insert(dest_.begin() + first, Dest{kDestNone, r, 0});
+            dest_.insert(dest_.begin() + first, Dest{kDestNone, r, 0, ws_, we_});
         } else if (asked_.size() == first + 1) {
             asked_.back().chain = -1;
         }
@@ -385,6 +459,14 @@ private:
                 }
             }
         }
+    }
+
+    // Rings asked per round for the current window size (speculation depth).
+    int spec_depth() const {
+        const int64_t m = we_ - ws_ + 1;
+        if (m <= 128) return 4;
+        if (m <= 512) return 2;
+        return 1;
     }
 
     void begin_climb(const Val &v) {
@@ -499,6 +581,7 @@ private:
     bool dropped_[2] = {false, false};
     std::vector<Ring> rings_;
     std::vector<Dest> dest_;
+    GridCache grid_;
     int32_t next_chain_ = 0;
 };
 
