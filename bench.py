@@ -51,6 +51,8 @@ def parse():
                          "ring (BU-ring sized windows), mix (all TD layers)")
     ap.add_argument("--case-pairs", type=int, default=8)
     ap.add_argument("--plain", action="store_true", help="also time the one-window-per-launch form")
+    ap.add_argument("--kernel-opt", type=int, default=0,
+                    help="ISYCOS_OPT_KERNEL: 0 auto, 1 brute force only, 2 sorted path")
     return ap.parse_args()
 
 
@@ -252,6 +254,12 @@ def case_windows(name, ids, length, rng):
         for a, b in ids:
             for t in range(0, 200 * 16, 16):
                 xs.append(a); ys.append(b); starts.append(t); sizes.append(2048)
+    elif name == "small":
+        for a, b in ids:
+            for _ in range(4000):
+                m = int(np.exp(rng.uniform(np.log(32), np.log(128))))
+                t = int(rng.integers(0, length - m))
+                xs.append(a); ys.append(b); starts.append(t); sizes.append(m)
     elif name == "ring":
         for a, b in ids:
             for _ in range(2000):
@@ -276,6 +284,7 @@ def kernel_case(args):
     pairs = make_pairs(0, args.case_pairs, args.length)
     ctx = api.isycos_create(0, 0)
     ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
+    api.isycos_set_option(ctx, api.OPT_KERNEL, args.kernel_opt)
     w = case_windows(args.kernel_case, ids, args.length, np.random.default_rng(5))
     for _ in range(args.warmup):
         api.isycos_mi_windows(ctx, w, 4)
@@ -291,7 +300,8 @@ def kernel_case(args):
     f = clocks["sm_mhz"] or 2070.0
     peak = n_sm * 4 * 32 * f * 1e6
     ach = OPS_PER_PAIR * pairs_per_launch / (ms / 1e3)
-    line = {"kernel_case": args.kernel_case, "windows": int(len(w)), "ms_per_launch": round(ms, 4),
+    line = {"kernel_case": args.kernel_case, "kernel_opt": args.kernel_opt, "windows": int(len(w)),
+            "ms_per_launch": round(ms, 4),
             "evals_per_s": round(len(w) / (ms / 1e3), 1),
             "pairs_per_s": round(pairs_per_launch / (ms / 1e3), 1),
             "roofline": {"bound": "alu", "achieved": round(ach / 1e9, 1), "peak": round(peak / 1e9, 1),
@@ -372,7 +382,11 @@ def main():
     st = api.isycos_get_stats(ctx)
     split = {k: round(v * 1e3 / args.steps, 2) for k, v in SPLIT.items()}
     total_ms = sum(times)
-    windows = st["windows"]
+    # value: window MIs that the searches' decisions read (the sequential algorithms' count,
+    # the unit of the oracle baseline); windows evaluated on the GPU including speculative
+    # ones are reported beside it
+    windows = st["decided_windows"]
+    gpu_windows = st["windows"]
     pairs_cnt = st["pairs"]
     if world > 1:
         t = torch.tensor([total_ms, windows, pairs_cnt], dtype=torch.float64, device="cuda")
@@ -398,6 +412,7 @@ def main():
         st0 = api.isycos_get_stats(ctx)
         nfound = run_step(api, ctx, eids, args.length)
         st1 = api.isycos_get_stats(ctx)
+        st0["windows"], st1["windows"] = st0["decided_windows"], st1["decided_windows"]
         for a, b in eids:
             api.isycos_drop_series(ctx, a)
             api.isycos_drop_series(ctx, b)
@@ -444,6 +459,8 @@ def main():
             "pairs_per_s": round(pairs_per_s, 1),
             "pairs_note": "brute-force-equivalent ordered pairs m(m-1) per evaluated window",
             "windows_per_step": int(windows_all / args.steps),
+            "gpu_windows_per_step": int(gpu_windows / args.steps),
+            "gpu_windows_per_s": round(gpu_windows / (total_ms / 1e3), 1),
             "found_windows_per_step": found,
             "ms_per_step_by_search": {"td": split["td_s"], "bu": split["bu_s"]},
             "incremental_windows_per_step": int(st["incr_windows"] / args.steps),

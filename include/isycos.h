@@ -121,6 +121,10 @@ typedef struct {
     int64_t incr_full_points; /* points whose neighbours the incremental update searched
                                again in full (the rest took +-1 count updates)       */
     int64_t queries_done;   /* served queries completed                               */
+    int64_t decided_windows;/* window scores read by the searches' decisions: the count
+                               of MI evaluations the sequential Algorithms 1 and 2
+                               make (speculatively evaluated windows that no decision
+                               read are in `windows` only)                          */
     double mi_kernel_ms;    /* device busy time of the batched MI kernels: the union of
                                their [start, stop] intervals (CUDA events on each
                                launching stream; concurrent launches counted once)    */
@@ -267,6 +271,8 @@ isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int
 #define ISYCOS_OPT_INCREMENTAL 2   /* searches: 0 off, 1 auto (default), 2 always           */
 #define ISYCOS_OPT_SERVE_SLOTS 3   /* serving: most queries admitted at once (default 64)   */
 #define ISYCOS_OPT_SERVE_QUEUE 4   /* serving: most queries waiting (default 100000)        */
+#define ISYCOS_OPT_LANES 5         /* searches: most engine lanes (host thread + stream)
+                                      (default: half the host cores, at most 8)              */
 isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
 
 /* Window MI that allocates nothing.  The paper has no counterpart: this entry point

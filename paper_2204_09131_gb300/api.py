@@ -31,6 +31,7 @@ OPT_KERNEL = 1
 OPT_INCREMENTAL = 2
 OPT_SERVE_SLOTS = 3
 OPT_SERVE_QUEUE = 4
+OPT_LANES = 5
 
 
 class IsycosError(RuntimeError):
@@ -67,7 +68,7 @@ class isycos_stats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("incr_windows", ctypes.c_int64), ("incr_full_points", ctypes.c_int64),
-                ("queries_done", ctypes.c_int64),
+                ("queries_done", ctypes.c_int64), ("decided_windows", ctypes.c_int64),
                 ("mi_kernel_ms", ctypes.c_double), ("mi_kernel_launches", ctypes.c_int64)]
 
 

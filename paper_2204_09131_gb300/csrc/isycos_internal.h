@@ -25,21 +25,26 @@ struct WorkItem {
 };
 
 // Work layout of one persistent launch: items sorted by size bucket, largest bucket first.
-// A job is one item (large windows, all warps of the CTA) or several items of one
-// bucket (small windows, `wpw` warps each).
+// Windows of more than 64 points are CTA jobs: one item (large windows, all warps of the CTA)
+// or several items of one bucket (`wpw` warps each).  Windows of at most 64 points (bucket
+// slots >= kSmallSlot) are taken one per warp, with no CTA barrier, once a CTA runs out of
+// CTA jobs.
+constexpr int kSmallSlot = kBuckets - 7;   // m <= 2^6
 struct BucketTable {
-    int32_t total_jobs;
+    int32_t total_jobs;          // CTA jobs
     int32_t n_items;
+    int32_t small_first;         // first item taken by single warps
+    int32_t pad;
     int32_t item_off[kBuckets];  // first item of bucket slot q
     int32_t count[kBuckets];     // items in bucket slot q
-    int32_t job_off[kBuckets];   // first job of bucket slot q
+    int32_t job_off[kBuckets];   // first CTA job of bucket slot q
     int32_t wpw[kBuckets];       // warps per item in bucket slot q
 };
 
 struct BatchArgs {
     const WorkItem *items;
     const BucketTable *table;
-    int32_t *queue;              // persistent work counter (zeroed before launch)
+    int32_t *queue;              // two work counters, CTA jobs and warp items (zeroed)
     const long long *psi_fx;
     const long long *log_fx;
     isycos_mi_out *out;
@@ -48,6 +53,7 @@ struct BatchArgs {
     int32_t *c;
     int32_t k;
     int32_t nt;                  // threads per CTA of the launch
+    int32_t sort_min;            // windows of at least this size take the sorted path
 };
 
 // Device-side preparation of a window list held in device memory.
@@ -88,23 +94,66 @@ inline int bucket_slot(int m) {
 }
 
 // Warps per item for bucket slot q in a CTA of nt threads.
-inline int warps_per_item(int q, int nt) {
-    int w = nt / 32;
-    int b = kBuckets - 1 - q;
-    int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
+__host__ __device__ inline int warps_per_item(int q, int nt) {
+    const int w = nt / 32;
+    const int b = kBuckets - 1 - q;
+    const int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
     int wpw = 1;
     while (wpw < need && wpw < w) wpw *= 2;
     return wpw;
 }
 
-// Shared memory of a batched launch whose largest window has max_m points.
-inline size_t batched_smem(int max_m, int nt) {
-    size_t a = (size_t)max_m * 8;
-    size_t b = (size_t)nt * kPoints * 8;   // all slots of the small-window buckets
-    return a > b ? a : b;
+// Fill the bucket table from the per-slot item counts (same layout on host and device).
+__host__ __device__ inline void fill_bucket_table(BucketTable *T, const int32_t *count, int nt) {
+    const int W = nt / 32;
+    int items = 0, jobs = 0;
+    for (int q = 0; q < kBuckets; ++q) {
+        const int wpw = q < kSmallSlot ? warps_per_item(q, nt) : 1;
+        T->item_off[q] = items;
+        T->count[q] = count[q];
+        T->job_off[q] = jobs;
+        T->wpw[q] = wpw;
+        items += count[q];
+        if (q < kSmallSlot) jobs += (count[q] + (W / wpw) - 1) / (W / wpw);
+    }
+    T->total_jobs = jobs;
+    T->n_items = items;
+    T->small_first = T->item_off[kSmallSlot];
+    T->pad = 0;
 }
 
-// Threads per CTA chosen for a batch whose largest window has max_m points.
-inline int batched_threads(int max_m) { return max_m > 8192 ? 1024 : 256; }
+// CTAs a launch needs at most: its CTA jobs plus enough warps for the small windows.
+inline int batched_grid_need(const BucketTable &T, int nt) {
+    const int W = nt / 32;
+    return T.total_jobs + (T.n_items - T.small_first + W - 1) / W;
+}
+
+// Largest window of the sorted path (its sort keys and records share the CTA's shared memory).
+constexpr int kSortMax = 4096;
+
+// Sorted path layout in shared memory after the window's m float2 values: the sort keys
+// (8 bytes per slot, the slot count rounded up to a power of two) then the x-ordered records
+// (16 bytes per point).
+__host__ __device__ inline size_t sorted_off(int m) { return ((size_t)m * 8 + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t sorted_smem(int m) {
+    int n = 1;
+    while (n < m) n <<= 1;
+    return sorted_off(m) + (size_t)8 * n + (size_t)16 * m;
+}
+
+// Shared memory of a batched launch whose largest window has max_m points; max_sorted is the
+// largest window that takes the sorted path (0: none).
+inline size_t batched_smem(int max_m, int nt, int max_sorted = 0) {
+    size_t a = (size_t)max_m * 8;
+    size_t b = (size_t)nt * kPoints * 8;   // all slots of the small-window buckets
+    size_t c = max_sorted > 0 ? sorted_smem(max_sorted) : 0;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+// Threads per CTA chosen for a batch whose largest window has max_m points (the sorted path
+// runs one window per CTA: more warps hide its dependent loads).
+inline int batched_threads(int max_m, int max_sorted = 0) {
+    return (max_m > 8192 || max_sorted > 0) ? 1024 : 256;
+}
 
 }  // namespace isy

@@ -81,15 +81,14 @@ __device__ __forceinline__ void write_result(isycos_mi_out *o, int k, int m, lon
     o->s_log = s_log;
 }
 
-// One 64-point block of a window staged in shared memory `s` (m points): all of a2-a5 for
-// points base + p * 32 + lane, p < kPoints.  Adds the block's sums to acc_psi / acc_log.
-template <int K1>
+// One block of 32 * P points of a window staged in shared memory `s` (m points): all of
+// a2-a5 for points base + p * 32 + lane, p < P.  Adds the block's sums to acc_psi / acc_log.
+template <int K1, int P = kPoints>
 __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, int base,
                                           int lane, const long long *__restrict__ psi_fx,
                                           const long long *__restrict__ log_fx,
                                           long long &acc_psi, long long &acc_log,
                                           int32_t *nx_out, int32_t *ny_out, int32_t *c_out) {
-    constexpr int P = kPoints;
     const float kInf = __int_as_float(0x7f800000);
     float xi[P], yi[P];
     bool val[P];
@@ -225,6 +224,189 @@ __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, i
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Sub-quadratic path for one large window (all threads of the CTA), the sorted-strip form of
+// the box-assisted search of Sec. 7.1: the window's points are sorted by x; each point's
+// neighbours are searched outward along the sorted order, nearest x first, until the x
+// distance on both sides exceeds the current k+1-th distance (no farther point can enter,
+// since d >= |dx|); the marginal counts are ranges of the x- and y-sorted values found by
+// binary search, because fl(|x_i - x_j|) is monotone along the sorted order.  Candidates
+// arrive out of time order, so the neighbour list compares (d, j) lexicographically.  Every
+// comparison is the same binary32 operation as in the brute-force path: results are equal.
+// ---------------------------------------------------------------------------------------
+
+// Order-preserving key of a float (-0 and +0 share a key).
+__device__ __forceinline__ uint32_t fkey(float f) {
+    const uint32_t u = __float_as_uint(f == 0.0f ? 0.0f : f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+template <int NT, typename T>
+__device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all threads
+    for (int k2 = 2; k2 <= N; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += NT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const T a = k[i], b = k[ixj];
+                    const bool up = (i & k2) == 0;
+                    if ((a > b) == up) {
+                        k[i] = b;
+                        k[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+template <int K1>
+__device__ __forceinline__ void insert_lex(float (&bd)[K1], int (&bj)[K1], float d, int j) {
+    bd[K1 - 1] = d;
+    bj[K1 - 1] = j;
+#pragma unroll
+    for (int r = K1 - 1; r > 0; --r) {
+        const bool sw = bd[r] < bd[r - 1] || (bd[r] == bd[r - 1] && bj[r] < bj[r - 1]);
+        const float a0 = bd[r - 1], a1 = bd[r];
+        const int b0 = bj[r - 1], b1 = bj[r];
+        bd[r - 1] = sw ? a1 : a0;
+        bd[r] = sw ? a0 : a1;
+        bj[r - 1] = sw ? b1 : b0;
+        bj[r] = sw ? b0 : b1;
+    }
+}
+
+__host__ __device__ inline int pow2_ceil(int m) {
+    int n = 1;
+    while (n < m) n <<= 1;
+    return n;
+}
+
+template <int K1, int NT>
+__device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned char *scratch,
+                                  const long long *__restrict__ psi_fx,
+                                  const long long *__restrict__ log_fx, long long &acc_psi,
+                                  long long &acc_log, int32_t *nx_out, int32_t *ny_out,
+                                  int32_t *c_out) {
+    const float kInf = __int_as_float(0x7f800000);
+    const int N = pow2_ceil(m);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
+    float4 *rec = reinterpret_cast<float4 *>(scratch + (size_t)8 * N);
+    for (int i = threadIdx.x; i < N; i += NT)
+        keys[i] = i < m ? (((unsigned long long)fkey(s[i].x) << 32) | (unsigned)i) : ~0ull;
+    __syncthreads();
+    bitonic_sort<NT>(keys, N);
+    for (int t = threadIdx.x; t < m; t += NT) {
+        const int j = (int)(keys[t] & 0xffffffffu);
+        rec[t] = make_float4(s[j].x, s[j].y, __int_as_float(j), 0.0f);
+    }
+    __syncthreads();
+    float *ys = reinterpret_cast<float *>(keys);   // the keys are no longer needed
+    for (int i = threadIdx.x; i < N; i += NT) ys[i] = i < m ? s[i].y : kInf;
+    __syncthreads();
+    bitonic_sort<NT>(ys, N);
+
+    for (int t = threadIdx.x; t < m; t += NT) {
+        const float4 me = rec[t];
+        const float xi = me.x, yi = me.y;
+        const int ji = __float_as_int(me.z);
+        float bd[K1];
+        int bj[K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            bd[r] = kInf;
+            bj[r] = 0x7fffffff;
+        }
+        insert_lex<K1>(bd, bj, 0.0f, ji);   // the point itself (d = 0)
+        int lo = t - 1, hi = t + 1;
+        float xlo = lo >= 0 ? rec[lo].x : 0.0f, xhi = hi < m ? rec[hi].x : 0.0f;
+        bool alo = lo >= 0, ahi = hi < m;
+        while (alo || ahi) {
+            const bool take_lo = alo && (!ahi || (xi - xlo) <= (xhi - xi));
+            const int u = take_lo ? lo : hi;
+            const float cx = take_lo ? xlo : xhi;
+            const float ax = fabsf(xi - cx);
+            if (ax > bd[K1 - 1]) {            // nothing farther on this side can enter
+                if (take_lo) alo = false;
+                else ahi = false;
+                continue;
+            }
+            const float4 c = rec[u];
+            const float d = fmaxf(ax, fabsf(yi - c.y));
+            const int jj = __float_as_int(c.z);
+            if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
+            if (take_lo) {
+                --lo;
+                alo = lo >= 0;
+                if (alo) xlo = rec[lo].x;
+            } else {
+                ++hi;
+                ahi = hi < m;
+                if (ahi) xhi = rec[hi].x;
+            }
+        }
+        float dxm = 0.0f, dym = 0.0f;
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            const float2 v = s[bj[r]];
+            dxm = fmaxf(dxm, fabsf(xi - v.x));
+            dym = fmaxf(dym, fabsf(yi - v.y));
+        }
+        // n_x: the x-sorted range around position t where fabsf(x_i - x) <= d_x
+        int l0 = 0, l1 = t;
+        while (l0 < l1) {
+            const int mid = (l0 + l1) >> 1;
+            if (fabsf(xi - rec[mid].x) <= dxm) l1 = mid;
+            else l0 = mid + 1;
+        }
+        int r0 = t, r1 = m - 1;
+        while (r0 < r1) {
+            const int mid = (r0 + r1 + 1) >> 1;
+            if (fabsf(xi - rec[mid].x) <= dxm) r0 = mid;
+            else r1 = mid - 1;
+        }
+        const int cx = r0 - l0 + 1;
+        // n_y: the same on the y-sorted values, around the first value >= y_i
+        int p0 = 0, p1 = m;
+        while (p0 < p1) {
+            const int mid = (p0 + p1) >> 1;
+            if (ys[mid] < yi) p0 = mid + 1;
+            else p1 = mid;
+        }
+        const int piv = p0;
+        int q0 = 0, q1 = piv;
+        while (q0 < q1) {
+            const int mid = (q0 + q1) >> 1;
+            if (fabsf(yi - ys[mid]) <= dym) q1 = mid;
+            else q0 = mid + 1;
+        }
+        int w0 = piv, w1 = m - 1;
+        while (w0 < w1) {
+            const int mid = (w0 + w1 + 1) >> 1;
+            if (fabsf(yi - ys[mid]) <= dym) w0 = mid;
+            else w1 = mid - 1;
+        }
+        const int cy = w0 - q0 + 1;
+        // multiplicity of (x_i, y_i)
+        int cc = 0;
+#pragma unroll
+        for (int r = 0; r < K1; ++r) cc += bd[r] == 0.0f ? 1 : 0;
+        if (bd[K1 - 1] == 0.0f) {
+            cc = 1;
+            for (int u = t - 1; u >= 0 && rec[u].x == xi; --u) cc += rec[u].y == yi ? 1 : 0;
+            for (int u = t + 1; u < m && rec[u].x == xi; ++u) cc += rec[u].y == yi ? 1 : 0;
+        }
+        const int nxv = cx - 1, nyv = cy - 1;
+        acc_psi += __ldg(psi_fx + nxv) + __ldg(psi_fx + nyv);
+        acc_log += __ldg(log_fx + cc);
+        if (nx_out) {
+            nx_out[ji] = nxv;
+            ny_out[ji] = nyv;
+            c_out[ji] = cc;
+        }
+    }
+}
+
 // Persistent, size-bucketed batch: CTAs take jobs from a counter; a job is one large window
 // (all warps) or several small windows of one bucket (wpw warps each).
 template <int K1, int NT>
@@ -267,9 +449,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                 nyo = a.ny + it.pts;
                 co = a.c + it.pts;
             }
-            const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
-            for (int b = sub; b < nblk; b += wpw)
-                ksg_block<K1>(s, it.m, b * kBlockPts, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            if (per_job == 1 && it.m >= a.sort_min && it.m <= kSortMax) {
+                ksg_window_sorted<K1, NT>(s, it.m, reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m),
+                                          a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            } else {
+                const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
+                for (int b = sub; b < nblk; b += wpw)
+                    ksg_block<K1>(s, it.m, b * kBlockPts, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            }
             lp = warp_sum64(lp);
             ll = warp_sum64(ll);
             if (lane == 0) {
@@ -280,6 +467,33 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         __syncthreads();
         if (has && sub == 0 && lane == 0)
             write_result(a.out + it.out, a.k, it.m, acc_psi[slot], acc_log[slot], a.psi_fx, a.log_fx);
+    }
+    // Small windows (m <= 64): one warp each, staged in the warp's own slice, no CTA barrier.
+    float2 *ws = tile + warp * kBlockPts;
+    const int first = T->small_first, last = T->n_items;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(a.queue + 1, 1);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (first + idx >= last) break;
+        const WorkItem it = a.items[first + idx];
+        __syncwarp();
+        for (int i = lane; i < it.m; i += 32) ws[i] = make_float2(it.x[i], it.y[i]);
+        __syncwarp();
+        long long lp = 0, ll = 0;
+        int32_t *nxo = nullptr, *nyo = nullptr, *co = nullptr;
+        if (a.nx && it.pts >= 0) {
+            nxo = a.nx + it.pts;
+            nyo = a.ny + it.pts;
+            co = a.c + it.pts;
+        }
+        if (it.m <= 32)
+            ksg_block<K1, 1>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+        else
+            ksg_block<K1, 2>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+        lp = warp_sum64(lp);
+        ll = warp_sum64(ll);
+        if (lane == 0) write_result(a.out + it.out, a.k, it.m, lp, ll, a.psi_fx, a.log_fx);
     }
 }
 
@@ -372,24 +586,7 @@ __global__ void prep_classify_kernel(PrepArgs a) {
 
 __global__ void prep_table_kernel(PrepArgs a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    BucketTable *T = a.table;
-    const int W = a.nt / 32;
-    int items = 0, jobs = 0;
-    for (int q = 0; q < kBuckets; ++q) {
-        const int b = kBuckets - 1 - q;
-        const int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
-        int wpw = 1;
-        while (wpw < need && wpw < W) wpw *= 2;
-        const int n = a.bucket_count[q];
-        T->item_off[q] = items;
-        T->count[q] = n;
-        T->job_off[q] = jobs;
-        T->wpw[q] = wpw;
-        items += n;
-        jobs += (n + (W / wpw) - 1) / (W / wpw);
-    }
-    T->total_jobs = jobs;
-    T->n_items = items;
+    fill_bucket_table(a.table, a.bucket_count, a.nt);
 }
 
 __global__ void prep_scatter_kernel(PrepArgs a) {

@@ -90,7 +90,7 @@ __global__ void noalloc_classify(NoallocPrep a) {
     const bool ok = m >= a.k + 1 && m <= a.max_m && s >= 0 && s + m <= a.n;
     if (!ok) {
         ctl_slot(a.scratch)[i] = -1;
-        atomicOr(ctl_counts(a.scratch) + kBuckets + 1, 1);
+        atomicOr(ctl_counts(a.scratch) + kBuckets + 2, 1);
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         a.out[i].mi = nan;
         a.out[i].h_w = nan;
@@ -107,24 +107,7 @@ __global__ void noalloc_classify(NoallocPrep a) {
 
 __global__ void noalloc_table(NoallocPrep a) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    BucketTable *T = ctl_table(a.scratch);
-    const int32_t *count = ctl_counts(a.scratch);
-    const int W = a.nt / 32;
-    int items = 0, jobs = 0;
-    for (int q = 0; q < kBuckets; ++q) {
-        const int b = kBuckets - 1 - q;
-        const int need = ((1 << b) + kBlockPts - 1) / kBlockPts;
-        int wpw = 1;
-        while (wpw < need && wpw < W) wpw *= 2;
-        T->item_off[q] = items;
-        T->count[q] = count[q];
-        T->job_off[q] = jobs;
-        T->wpw[q] = wpw;
-        items += count[q];
-        jobs += (count[q] + (W / wpw) - 1) / (W / wpw);
-    }
-    T->total_jobs = jobs;
-    T->n_items = items;
+    fill_bucket_table(ctl_table(a.scratch), ctl_counts(a.scratch), a.nt);
 }
 
 __global__ void noalloc_scatter(NoallocPrep a) {
@@ -223,7 +206,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     pa.nt = nt;
     pa.scratch = d.scratch;
     pa.out = d_out;
-    // counters, error flag and work counter start at zero on every call
+    // bucket counters, the two work counters and the error flag start at zero on every call
     if (cudaMemsetAsync(d.scratch, 0, 128, st) != cudaSuccess) return ISYCOS_E_CUDA;
     const int blocks = (int)((n_w + 255) / 256);
     noalloc_classify<<<blocks, 256, 0, st>>>(pa);
@@ -241,6 +224,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     a.nx = a.ny = a.c = nullptr;
     a.k = k;
     a.nt = nt;
+    a.sort_min = INT32_MAX;   // brute-force path only
     if (launch_batched(a, n_sm * per_sm, smem, st) != cudaSuccess) return ISYCOS_E_CUDA;
     return ISYCOS_OK;
 }

@@ -109,22 +109,16 @@ isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k) {
     return ISYCOS_OK;
 }
 
-// Build the persistent launch's bucket table for items already sorted by slot.
-static void build_table(BucketTable &T, const int32_t *count, int nt) {
-    const int W = nt / 32;
-    int items = 0, jobs = 0;
-    for (int q = 0; q < kBuckets; ++q) {
-        const int wpw = warps_per_item(q, nt);
-        T.item_off[q] = items;
-        T.count[q] = count[q];
-        T.job_off[q] = jobs;
-        T.wpw[q] = wpw;
-        items += count[q];
-        jobs += (count[q] + (W / wpw) - 1) / (W / wpw);
-    }
-    T.total_jobs = jobs;
-    T.n_items = items;
+// Smallest window that takes the sorted (sub-quadratic) path: ISYCOS_OPT_KERNEL 1 keeps
+// everything on the brute-force path; 0 (auto) and 2 send the windows that run one per CTA
+// (more than 1024 points with 1024 threads per CTA) up to kSortMax to the sorted path.
+int sort_threshold(const isycos_ctx *ctx) {
+    if (ctx->opt_kernel == 1) return INT32_MAX;
+    return 1025;
 }
+
+// Build the persistent launch's bucket table for items already sorted by slot.
+static void build_table(BucketTable &T, const int32_t *count, int nt) { fill_bucket_table(&T, count, nt); }
 
 static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
     std::lock_guard<std::mutex> g(ctx->launch_mu);
@@ -164,20 +158,22 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
                           cudaStream_t st) {
     if (n <= 0) return ISYCOS_OK;
     if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
-    int max_m = 0;
+    int max_m = 0, max_sorted = 0;
+    const int sort_min = sort_threshold(ctx);
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
     std::vector<int32_t> &slot = L.h_slot;
     slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         max_m = std::max(max_m, w[i].m);
+        if (w[i].m >= sort_min && w[i].m <= kSortMax) max_sorted = std::max(max_sorted, w[i].m);
         pairs += (int64_t)w[i].m * (w[i].m - 1);
         slot[i] = bucket_slot(w[i].m);
         count[slot[i]]++;
         total_pts += w[i].m;
     }
-    const int nt = batched_threads(max_m);
-    const size_t smem = batched_smem(max_m, nt);
+    const int nt = batched_threads(max_m, max_sorted);
+    const size_t smem = batched_smem(max_m, nt, max_sorted);
     isycos_status rc;
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
 
@@ -213,11 +209,11 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
         if ((rc = dev_reserve(ctx, L.d_c, 4 * total_pts))) return rc;
     }
     cudaError_t e = cudaMemcpyAsync(L.d_items.p, stage, stage_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.d_queue.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.d_queue.p, 0, 8, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "staging the window list");
 
     int grid;
-    if ((rc = launch_grid(ctx, k, nt, smem, T.total_jobs, &grid))) return rc;
+    if ((rc = launch_grid(ctx, k, nt, smem, batched_grid_need(T, nt), &grid))) return rc;
     BatchArgs a;
     a.items = reinterpret_cast<const WorkItem *>(reinterpret_cast<unsigned char *>(L.d_items.p) + tab_bytes);
     a.table = reinterpret_cast<const BucketTable *>(L.d_items.p);
@@ -230,6 +226,7 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     a.c = nx ? reinterpret_cast<int32_t *>(L.d_c.p) : nullptr;
     a.k = k;
     a.nt = nt;
+    a.sort_min = sort_min;
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
@@ -278,6 +275,14 @@ isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out) {
     }
     *out = ctx->lanes[i];
     return ISYCOS_OK;
+}
+
+void lane_release(isycos_ctx *ctx, Lane &L) {
+    cudaStreamSynchronize(L.stream);
+    DevBuf *bufs[] = {&L.d_items, &L.d_queue, &L.d_out, &L.d_nx, &L.d_ny, &L.d_c,
+                      &L.d_chain_desc, &L.d_chain_steps, &L.d_chain_state,
+                      &L.d_chain_recomp, &L.d_chain_out};
+    for (DevBuf *b : bufs) dev_release(ctx, *b);
 }
 
 static void free_lane(isycos_ctx *ctx, Lane *L) {
@@ -585,8 +590,10 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     isycos_status rc;
     if ((rc = sync_series_table(ctx, st))) return rc;
-    const int nt = batched_threads(max_m);
-    const size_t smem = batched_smem(max_m, nt);
+    const int sort_min = sort_threshold(ctx);
+    const int max_sorted = max_m >= sort_min ? std::min(max_m, kSortMax) : 0;
+    const int nt = batched_threads(max_m, max_sorted);
+    const size_t smem = batched_smem(max_m, nt, max_sorted);
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_dev_items, sizeof(WorkItem) * n_w))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_slot, 4 * n_w))) return rc;
@@ -612,7 +619,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     pa.status = reinterpret_cast<int32_t *>(ctx->d_status.p);
     pa.out = d_out;
     cudaError_t e = cudaMemsetAsync(ctx->d_bcount.p, 0, 4 * kBuckets, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_dev_queue.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_dev_queue.p, 0, 8, st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_prep(pa, st, &launches);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "window preparation");
@@ -628,6 +635,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.nx = a.ny = a.c = nullptr;
     a.k = k;
     a.nt = nt;
+    a.sort_min = sort_min;
     e = launch_batched(a, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
     add_stats(ctx, n_w, 0, launches + 1, 1, 0);
@@ -752,6 +760,10 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) 
         case ISYCOS_OPT_SERVE_QUEUE:
             if (value < 1 || value > 1 << 24) break;
             ctx->serve_queue = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_LANES:
+            if (value < 1 || value > 64) break;
+            ctx->max_lanes = (int)value;
             return ISYCOS_OK;
         default:
             return fail(ctx, ISYCOS_E_INVAL, "unknown option %d", option);

@@ -119,10 +119,16 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
 // Lane i of the context (created on first use; lane 0 runs on ctx->stream).
 isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out);
 
+// Free a lane's device work buffers (they are allocated again on next use).
+void lane_release(isycos_ctx *ctx, Lane &L);
+
 void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches,
                int64_t batches, int64_t incr_windows);
 
 cudaStream_t pick_stream(isycos_ctx *ctx, void *s);
+
+// Smallest window size of the sorted (sub-quadratic) MI path for this context.
+int sort_threshold(const isycos_ctx *ctx);
 
 // A window sequence of one pair for the incremental kernel: result i goes to out[out_idx[i]]
 // (out_idx < 0: evaluated for its state only, result dropped).

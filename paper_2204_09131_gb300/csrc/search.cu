@@ -464,8 +464,8 @@ private:
     // Rings asked per round for the current window size (speculation depth).
     int spec_depth() const {
         const int64_t m = we_ - ws_ + 1;
-        if (m <= 128) return 4;
-        if (m <= 512) return 2;
+        if (m <= 256) return 4;
+        if (m <= 2048) return 2;
         return 1;
     }
 
@@ -791,7 +791,7 @@ isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     // Independent queries split over engine lanes, one host thread per lane: each thread runs
     // its machines' rounds on its own stream, so that the sequential decision logic of many
     // queries proceeds in parallel and their small batches overlap on the GPU.
-    const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 7) / 8));
+    const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 3) / 4));
     std::vector<Lane *> lanes((size_t)n_lanes);
     for (int i = 0; i < n_lanes; ++i)
         if ((rc = get_lane(ctx, i, &lanes[i]))) return rc;
@@ -810,6 +810,12 @@ isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     for (isycos_status s1 : st)
         if (s1) return s1;
     isycos_status result = ISYCOS_OK;
+    {
+        int64_t decided = 0;
+        for (SearchMachine *m : ms) decided += m->evals;
+        std::lock_guard<std::mutex> g2(ctx->stats_mu);
+        ctx->stats.decided_windows += decided;
+    }
     for (int64_t q = 0; q < n_q; ++q) {
         const auto &f = ms[q]->found;
         n_out[q] = (int64_t)f.size();

@@ -1,12 +1,14 @@
 // Serving loop: continuous batching of correlation-search queries.
 //
 // Queries (pair, time range, parameters) are submitted from any thread and receive a ticket.
-// A library thread admits queued queries while the number of running queries stays below
-// the slot limit and their estimated device work memory fits in what the context's budget
-// leaves after the resident series.  Every round it collects the pending window requests of
-// all running queries (TD layer grids, BU rings), evaluates them in one persistent GPU batch,
-// hands each query its results and retires the queries that finished; queries that arrive
-// meanwhile join at the next round.  The decisions of a query do not depend on which other
+// Library worker threads (one engine lane each: a CUDA stream with its own buffers) admit
+// queued queries while the number of running queries stays below the slot limit and their
+// estimated device work memory fits in what the context's budget leaves after the resident
+// series; an admitted query joins the least loaded worker.  Every round a worker collects the
+// pending window requests of its running queries (TD layer grids, BU rings), evaluates them in
+// one persistent GPU batch, hands each query its results and retires the queries that
+// finished; queries that arrive meanwhile join at the next round.  Workers run concurrently,
+// so their batches overlap on the GPU.  The decisions of a query do not depend on which other
 // queries share its batches, so a query's result is the same alone and in the mix.
 #include <chrono>
 #include <condition_variable>
@@ -23,7 +25,22 @@ using Clock = std::chrono::steady_clock;
 
 class Server {
 public:
-    explicit Server(isycos_ctx *ctx) : ctx_(ctx), th_([this] { loop(); }) {}
+    // Worker threads, each with its own engine lane (stream and buffers), each stepping its
+    // own share of the running queries; the lanes are separate from those of the searches.
+    explicit Server(isycos_ctx *ctx) : ctx_(ctx) {
+        int n = std::max(1, std::min(ctx->max_lanes, 8));
+        {
+            std::lock_guard<std::mutex> g(ctx->engine_mu);
+            cudaSetDevice(ctx->device);
+            for (int w = 0; w < n; ++w) {
+                Lane *L = nullptr;
+                if (get_lane(ctx, kServeLaneBase + w, &L) != ISYCOS_OK) break;
+                lanes_.push_back(L);
+            }
+        }
+        running_.resize(lanes_.size());
+        for (size_t w = 0; w < lanes_.size(); ++w) th_.emplace_back([this, w] { loop((int)w); });
+    }
 
     ~Server() {
         {
@@ -31,8 +48,10 @@ public:
             stop_ = true;
         }
         cv_.notify_all();
-        th_.join();
+        for (auto &t : th_) t.join();
     }
+
+    static constexpr int kServeLaneBase = 32;
 
     isycos_status submit(int32_t xs, int32_t ys, int64_t tb, int64_t te, const SearchParams &p,
                          uint64_t *ticket) {
@@ -115,6 +134,7 @@ private:
         double latency_ms = 0.0;
         isycos_status status = ISYCOS_OK;
         size_t bytes = 0;
+        int worker = 0;
     };
 
     // Device bytes the engine may need for this query's largest batch: a full TD layer grid
@@ -129,7 +149,8 @@ private:
         } else {
             windows = 8 * (int64_t)(p.t_max_idle + 1) + 2;
         }
-        return (size_t)windows * (sizeof(WorkItem) + sizeof(isycos_mi_out));
+        // twice: the engine's buffers grow by half their size at a time
+        return 2 * (size_t)windows * (sizeof(WorkItem) + sizeof(isycos_mi_out));
     }
 
     size_t capacity() const {
@@ -140,11 +161,18 @@ private:
         return ctx_->budget > fixed ? ctx_->budget - fixed : 0;
     }
 
+    size_t n_running() const {
+        size_t n = 0;
+        for (const auto &r : running_) n += r.size();
+        return n;
+    }
+
     void admit() {  // holds mu_
         const size_t cap = capacity();
-        while (!queue_.empty() && (int)running_.size() < ctx_->serve_slots) {
+        bool any = false;
+        while (!queue_.empty() && (int)n_running() < ctx_->serve_slots) {
             Query &q = *all_[queue_.front()];
-            if (reserved_ + q.bytes > cap && !running_.empty()) break;   // wait for memory
+            if (reserved_ + q.bytes > cap && n_running() > 0) break;   // wait for memory
             if (q.bytes > cap) {
                 q.state = kFailed;
                 q.status = ISYCOS_E_NOMEM;
@@ -155,57 +183,66 @@ private:
             q.sm = make_machine(q.xs, q.ys, q.tb, q.te, q.prm);
             q.state = kRunning;
             reserved_ += q.bytes;
-            running_.push_back(&q);
+            size_t w = 0;
+            for (size_t i = 1; i < running_.size(); ++i)
+                if (running_[i].size() < running_[w].size()) w = i;
+            q.worker = (int)w;
+            running_[w].push_back(&q);
+            any = true;
         }
+        if (any) cv_.notify_all();
     }
 
     void retire(Query *q, State st, isycos_status status) {  // holds mu_
         q->state = st;
         q->status = status;
         q->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - q->t_submit).count();
-        if (st == kDone) q->result = q->sm->found;
+        if (st == kDone) {
+            q->result = q->sm->found;
+            std::lock_guard<std::mutex> g(ctx_->stats_mu);
+            ctx_->stats.decided_windows += q->sm->evals;
+        }
         q->sm.reset();
         reserved_ -= q->bytes;
     }
 
-    void loop() {
+    void loop(int w) {
+        Lane &L = *lanes_[w];
+        cudaSetDevice(ctx_->device);
         std::vector<Query *> batch;
         std::vector<SearchMachine *> ms;
         std::vector<bool> finished;
+        auto &mine = running_[w];
         for (;;) {
             {
                 std::unique_lock<std::mutex> g(mu_);
-                for (size_t i = 0; i < running_.size();) {
-                    if (running_[i]->cancel) {
-                        retire(running_[i], kCanceled, ISYCOS_E_CANCELED);
-                        running_.erase(running_.begin() + i);
+                for (size_t i = 0; i < mine.size();) {
+                    if (mine[i]->cancel) {
+                        retire(mine[i], kCanceled, ISYCOS_E_CANCELED);
+                        mine.erase(mine.begin() + i);
                     } else {
                         ++i;
                     }
                 }
                 admit();
-                if (running_.empty()) {
+                if (mine.empty()) {
                     if (stop_) return;
-                    cv_.wait_for(g, std::chrono::milliseconds(50));
+                    if (L.d_items.p) lane_release(ctx_, L);   // idle: give the memory back
+                    cv_.wait_for(g, std::chrono::milliseconds(20));
                     continue;
                 }
                 if (stop_) {
-                    for (Query *q : running_) retire(q, kCanceled, ISYCOS_E_CANCELED);
-                    running_.clear();
+                    for (Query *q : mine) retire(q, kCanceled, ISYCOS_E_CANCELED);
+                    mine.clear();
                     return;
                 }
-                batch = running_;
+                batch = mine;
             }
             ms.clear();
             for (Query *q : batch) ms.push_back(q->sm.get());
             finished.assign(ms.size(), false);
-            isycos_status rc;
-            {
-                std::lock_guard<std::mutex> eg(ctx_->engine_mu);
-                cudaSetDevice(ctx_->device);
-                int64_t n = 0;
-                rc = step_machines(ctx_, *ctx_->lanes[0], ms, finished, ctx_->stream, &n);
-            }
+            int64_t n = 0;
+            const isycos_status rc = step_machines(ctx_, L, ms, finished, L.stream, &n);
             std::lock_guard<std::mutex> g(mu_);
             for (size_t i = 0; i < batch.size(); ++i) {
                 if (rc != ISYCOS_OK) {
@@ -217,9 +254,9 @@ private:
                 } else {
                     continue;
                 }
-                for (size_t r = 0; r < running_.size(); ++r)
-                    if (running_[r] == batch[i]) {
-                        running_.erase(running_.begin() + r);
+                for (size_t r = 0; r < mine.size(); ++r)
+                    if (mine[r] == batch[i]) {
+                        mine.erase(mine.begin() + r);
                         break;
                     }
             }
@@ -233,9 +270,10 @@ private:
     uint64_t next_ = 1;
     std::deque<uint64_t> queue_;
     std::unordered_map<uint64_t, std::unique_ptr<Query>> all_;
-    std::vector<Query *> running_;
+    std::vector<std::vector<Query *>> running_;   // per worker
+    std::vector<Lane *> lanes_;
     size_t reserved_ = 0;
-    std::thread th_;
+    std::vector<std::thread> th_;
 };
 
 static std::mutex g_server_create_mu;

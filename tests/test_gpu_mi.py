@@ -232,3 +232,32 @@ def test_stats_count_windows_and_pairs(ctx):
     assert s["windows"] == 3 and s["pairs"] == 100 * 99 + 200 * 199 + 50 * 49
     assert s["launches"] == 1 and s["mi_kernel_launches"] == 1 and s["mi_kernel_ms"] > 0
     api.isycos_drop_series(ctx, xs)
+
+
+def test_sorted_path_equals_brute_force(ctx):
+    """The sub-quadratic sorted-strip path (windows of 1025..4096 points) against the
+    brute-force path and the oracle, per point, on smooth, tied and degenerate data."""
+    api = _api()
+    n = 20000
+    x, y, _ = synth.planted_pair(8, 0, n)
+    base = synth.normal(synth.seed_for(204, 0), n).astype(np.float32)
+    cases = [(x, y), (synth.quantize(x), synth.quantize(y)),
+             (synth.quantize(x, 2.0), synth.quantize(y, 2.0)), (base, base.copy()),
+             (np.full(n, 2.5, np.float32), base), (np.round(base).astype(np.float32), -base)]
+    sizes = [1025, 1500, 2048, 3001, 4096]
+    starts = [11, 3000, 7000, 12000, 15000]
+    for ci, (xx, yy) in enumerate(cases):
+        xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
+        w = api.windows_array(xs, ys, starts, sizes)
+        res = {}
+        for opt in (1, 2):
+            api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+            res[opt] = api.isycos_mi_windows_points(ctx, w, 4)
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+        for a, b in zip(res[1], res[2]):
+            assert np.array_equal(a, b), ci
+        if ci < 3:
+            r = O.ksg_window(xx[3000:4500], yy[3000:4500], 4, points=False)
+            assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
+        api.isycos_drop_series(ctx, xs)
+        api.isycos_drop_series(ctx, ys)

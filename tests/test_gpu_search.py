@@ -213,11 +213,11 @@ def test_serving_concurrent_submitters_and_cancel(ctx):
 
 def test_serving_admission_under_a_small_budget():
     """A context whose budget leaves room for one query's work buffers at a time (each TD
-    query here needs about 180 KB: 2,501 windows of the s_w = 32 layer) still completes every
-    query, one after another, with the same results."""
+    query here is estimated at 360 KB: 2,501 windows of the s_w = 32 layer, twice for buffer
+    growth) still completes every query, one after another, with the same results."""
     api = _api()
     x, y, _ = synth.planted_pair(4, 11, 20000)
-    c = api.Context(0, mem_budget_bytes=(2 * 20000 * 4) + 2 * 8 * 16386 + 250_000)
+    c = api.Context(0, mem_budget_bytes=(2 * 20000 * 4) + 2 * 8 * 16386 + 500_000)
     try:
         a, b = api.isycos_put_series(c.h, x), api.isycos_put_series(c.h, y)
         prm = dict(k=4, s_min=32, s_max=256, mode=0)
@@ -257,3 +257,19 @@ def test_search_with_incremental_updates(ctx, opt, extra):
     mode = okw.pop("mode")
     ref, _ = (O.search_td if mode == 0 else O.search_bu)(x, y, **okw)
     _same(got, ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_decided_windows_equal_the_oracles_evaluations(ctx, mode):
+    """Batching evaluates extra (speculative) windows; the decisions read exactly the scores
+    the sequential algorithm computes, so the decided-window count equals the oracle's."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, pruning=1, seed=21)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    api.isycos_reset_stats(ctx)
+    api.isycos_search(ctx, xs, ys, 0, len(x), dict(kw, mode=mode))
+    st = api.isycos_get_stats(ctx)
+    _, n_evals = (O.search_td if mode == 0 else O.search_bu)(x, y, **kw)
+    assert st["decided_windows"] == n_evals
+    assert st["windows"] >= n_evals
