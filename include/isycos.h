@@ -97,10 +97,14 @@ typedef struct {
     int32_t h;           /* LAHC history length; <= 0: 8                                 */
     int32_t t_max_idle;  /* LAHC idle limit; < 0: 3                                      */
     int32_t p;           /* consecutive noise detections before pruning; <= 0: 3         */
-    int32_t mode;        /* 0: SYCOS_TD, 1: SYCOS_BU                                     */
+    int32_t mode;        /* 0: SYCOS_TD, 1: SYCOS_BU, 2: iSYCOS selection (Alg. 3)       */
     int32_t pruning;     /* 0 off, 1 noise pruning (Sec. 6) on                           */
     int32_t max_steps;   /* LAHC steps per climb; <= 0: 10000                            */
-    uint64_t seed;       /* seed of the LAHC history-index stream                        */
+    uint64_t seed;       /* seed of the LAHC history-index stream and of Alg. 3 sampling  */
+    int32_t sel_partitions; /* Alg. 3: M equal partitions of the range; <= 0: 20           */
+    int32_t sel_samples;    /* Alg. 3: m partitions sampled; <= 0: 6                       */
+    double sel_alpha;       /* Alg. 3: weight of the runtime factor; < 0: 0.5               */
+    double sel_rho;         /* Alg. 3: a window is small iff size <= rho * s_max; <= 0: 0.5 */
 } isycos_params;
 
 /* One correlated window found by a search.  32 bytes. */
@@ -240,6 +244,22 @@ isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
                                  const int64_t *t_end, const isycos_params *params,
                                  isycos_result_window *out, int64_t cap_per_query,
                                  int64_t *n_out);
+
+/* One search query: a pair, a range [t_begin, t_end) and its own parameters. */
+typedef struct {
+    int32_t xs;
+    int32_t ys;
+    int64_t t_begin;
+    int64_t t_end;
+    isycos_params params;
+} isycos_query;
+
+/* As isycos_search_many, with parameters per query (e.g. SYCOS_TD and SYCOS_BU queries of the
+ * same pairs in one call: their frontiers run concurrently and share the GPU).  Results of
+ * query i go to out + i * cap_per_query; n_out[i] receives their number. */
+isycos_status isycos_search_queries(isycos_ctx *ctx, int64_t n_q, const isycos_query *queries,
+                                    isycos_result_window *out, int64_t cap_per_query,
+                                    int64_t *n_out);
 
 /* Serving (continuous batching).  submit enqueues a search query and returns a ticket at
  * once; a library thread admits queued queries while device memory allows, merges the

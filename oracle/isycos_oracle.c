@@ -562,3 +562,113 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
     free(S.v);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* iSYCOS selection (Sec. 5.3, Algorithm 3, Eqs. effscore / normalizedeffscore) */
+/* ------------------------------------------------------------------------- */
+
+/* Normalised efficiency scores (Eqs. normalizeruntime, normalizedwindows,
+ * normalizedeffscore_TD / _BU): t~ = t / (t_TD + t_BU), n~L_TD = nL_TD / (nS_BU + nL_TD),
+ * n~S_BU = nS_BU / (nS_BU + nL_TD), nscore = alpha / t~ + (1 - alpha) n~.
+ * Readings: when both runtimes are 0 each normalised runtime is 1/2; when both window counts
+ * are 0 both normalised counts are 0. */
+void orc_nscores(double t_td, double t_bu, double nl_td, double ns_bu, double alpha,
+                 double *ns_td_out, double *ns_bu_out)
+{
+    double tt = t_td + t_bu;
+    double rt_td = tt > 0.0 ? t_td / tt : 0.5;
+    double rt_bu = tt > 0.0 ? t_bu / tt : 0.5;
+    double nn = ns_bu + nl_td;
+    double wl_td = nn > 0.0 ? nl_td / nn : 0.0;
+    double ws_bu = nn > 0.0 ? ns_bu / nn : 0.0;
+    *ns_td_out = alpha * (1.0 / rt_td) + (1.0 - alpha) * wl_td;
+    *ns_bu_out = alpha * (1.0 / rt_bu) + (1.0 - alpha) * ws_bu;
+}
+
+/* A scorer wrapper that adds up the pair comparisons m (m - 1) of every scored window: the
+ * deterministic "runtime" of a search. */
+typedef struct {
+    orc_score_fn f;
+    void *user;
+    double cost;
+} orc_cost_scorer;
+
+static int orc_cost_score(void *user, int64_t t_s, int64_t t_e, double *score, double *mi)
+{
+    orc_cost_scorer *c = (orc_cost_scorer *)user;
+    double m = (double)(t_e - t_s + 1);
+    c->cost += m * (m - 1.0);
+    return c->f(c->user, t_s, t_e, score, mi);
+}
+
+typedef struct {
+    int32_t partitions;   /* M, <= 0: 20                                   */
+    int32_t samples;      /* m, <= 0: 6 (the paper's experiments sample 6) */
+    double alpha;         /* weight of the runtime factor, < 0: 0.5         */
+    double rho;           /* small windows: size <= rho * s_max, <= 0: 0.5  */
+} orc_select_params;
+
+/* Algorithm 3: sample `samples` of `partitions` equal partitions of [t_begin, t_end), run
+ * SYCOS_TD and SYCOS_BU on each, score them (runtime = pair comparisons of the windows each
+ * search scores), and run the selected search on the whole range.  *selected = 0 (TD) or 1. */
+int orc_search_auto(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
+                    const orc_params *p, const orc_select_params *sp, orc_window *out,
+                    int64_t cap, int64_t *n_out, int64_t *n_evals, int32_t *selected,
+                    double *scores)
+{
+    int rc = orc_check_params(p, t_begin, t_end);
+    if (rc) return rc;
+    int32_t M = (sp && sp->partitions > 0) ? sp->partitions : 20;
+    int32_t ms = (sp && sp->samples > 0) ? sp->samples : 6;
+    double alpha = (sp && sp->alpha >= 0.0) ? sp->alpha : 0.5;
+    double rho = (sp && sp->rho > 0.0) ? sp->rho : 0.5;
+    int64_t N = t_end - t_begin;
+    if (ms > M) ms = M;
+    int64_t L = N / M;
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+    if (!idx) return ORC_ENOMEM;
+    for (int32_t i = 0; i < M; ++i) idx[i] = i;
+    /* Random sampling: partial Fisher-Yates shuffle driven by SplitMix64 outputs of the stream
+     * seed ^ 0x5E1EC7 (one draw per sampled partition). */
+    for (int32_t i = 0; i < ms; ++i) {
+        uint64_t r = orc_splitmix64_at(p->seed ^ 0x5E1EC7ULL, (uint64_t)i + 1);
+        int32_t j = i + (int32_t)(r % (uint64_t)(M - i));
+        int32_t t = idx[i]; idx[i] = idx[j]; idx[j] = t;
+    }
+    double t_td = 0.0, t_bu = 0.0, nl_td = 0.0, ns_bu = 0.0;
+    int64_t evals = 0;
+    orc_window *buf = (orc_window *)malloc(sizeof(orc_window) * 65536);
+    if (!buf) { free(idx); return ORC_ENOMEM; }
+    for (int32_t i = 0; i < ms && L > 0 && rc == ORC_OK; ++i) {
+        int64_t a = t_begin + (int64_t)idx[i] * L, b = a + L;
+        for (int alg = 0; alg < 2 && rc == ORC_OK; ++alg) {
+            orc_cost_scorer cs = {f, user, 0.0};
+            int64_t nw = 0, ne = 0;
+            rc = (alg == 0 ? orc_search_td : orc_search_bu)(orc_cost_score, &cs, a, b, p, buf, 65536,
+                                                             &nw, &ne);
+            if (rc) break;
+            evals += ne;
+            for (int64_t q = 0; q < nw; ++q) {
+                double size = (double)(buf[q].t_e - buf[q].t_s + 1);
+                int small = size <= rho * (double)p->s_max;
+                if (alg == 0 && !small) nl_td += 1.0;
+                if (alg == 1 && small) ns_bu += 1.0;
+            }
+            if (alg == 0) t_td += cs.cost; else t_bu += cs.cost;
+        }
+    }
+    free(buf);
+    free(idx);
+    if (rc) return rc;
+    t_td /= (double)ms;     /* average runtimes over the m partitions */
+    t_bu /= (double)ms;
+    double s_td, s_bu;
+    orc_nscores(t_td, t_bu, nl_td, ns_bu, alpha, &s_td, &s_bu);
+    if (scores) { scores[0] = s_td; scores[1] = s_bu; }
+    int32_t sel = s_td > s_bu ? 0 : 1;
+    if (selected) *selected = sel;
+    int64_t ne = 0;
+    rc = (sel == 0 ? orc_search_td : orc_search_bu)(f, user, t_begin, t_end, p, out, cap, n_out, &ne);
+    if (n_evals) *n_evals = evals + ne;
+    return rc;
+}

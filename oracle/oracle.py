@@ -104,6 +104,11 @@ class OrcSeriesScorer(ctypes.Structure):
     ]
 
 
+class OrcSelectParams(ctypes.Structure):
+    _fields_ = [("partitions", ctypes.c_int32), ("samples", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
 SCORE_FN = ctypes.CFUNCTYPE(
     ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
@@ -130,6 +135,12 @@ def lib():
             fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                            ctypes.POINTER(OrcParams), ctypes.POINTER(OrcWindow), ctypes.c_int64,
                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.orc_nscores.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_double)] * 2
+        L.orc_search_auto.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.POINTER(OrcParams), ctypes.POINTER(OrcSelectParams),
+                                      ctypes.POINTER(OrcWindow), ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -284,3 +295,32 @@ def search_bu(x_or_score, y=None, t_begin=0, t_end=None, **kw):
         if t_end is None:
             t_end = len(x_or_score)
     return _search("orc_search_bu", score, t_begin, t_end, params)
+
+
+def nscores(t_td, t_bu, nl_td, ns_bu, alpha=0.5):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().orc_nscores(t_td, t_bu, nl_td, ns_bu, alpha, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def search_auto(x, y, t_begin=0, t_end=None, partitions=20, samples=6, alpha=0.5, rho=0.5, **kw):
+    """Algorithm 3 (iSYCOS selection) over [t_begin, t_end); returns (windows, n_evals,
+    selected (0 TD / 1 BU), (nscore_TD, nscore_BU))."""
+    params = make_params(**kw)
+    score = series_scorer(x, y, params.k, params.score_kind)
+    if t_end is None:
+        t_end = len(x)
+    sp = OrcSelectParams(partitions, samples, alpha, rho)
+    cap = 1 << 16
+    out = (OrcWindow * cap)()
+    n_out, n_evals = ctypes.c_int64(), ctypes.c_int64()
+    sel = ctypes.c_int32()
+    sc = (ctypes.c_double * 2)()
+    fptr, user = score
+    rc = lib().orc_search_auto(fptr, ctypes.byref(user), t_begin, t_end, ctypes.byref(params),
+                               ctypes.byref(sp), out, cap, ctypes.byref(n_out), ctypes.byref(n_evals),
+                               ctypes.byref(sel), sc)
+    if rc != 0:
+        raise ValueError("orc_search_auto failed with %d" % rc)
+    wins = [(out[i].t_s, out[i].t_e, out[i].score, out[i].mi) for i in range(n_out.value)]
+    return wins, n_evals.value, sel.value, (sc[0], sc[1])

@@ -56,7 +56,14 @@ class isycos_params(ctypes.Structure):
                 ("delta_td", ctypes.c_int32), ("delta_bu", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("t_max_idle", ctypes.c_int32), ("p", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("pruning", ctypes.c_int32), ("max_steps", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("sel_partitions", ctypes.c_int32),
+                ("sel_samples", ctypes.c_int32), ("sel_alpha", ctypes.c_double),
+                ("sel_rho", ctypes.c_double)]
+
+
+class isycos_query(ctypes.Structure):
+    _fields_ = [("xs", ctypes.c_int32), ("ys", ctypes.c_int32), ("t_begin", ctypes.c_int64),
+                ("t_end", ctypes.c_int64), ("params", isycos_params)]
 
 
 class isycos_result_window(ctypes.Structure):
@@ -106,6 +113,7 @@ SIGNATURES = {
                              _I64, ctypes.POINTER(_I64)]),
     "isycos_search_many": (_I32, [_VP, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(isycos_params),
                                   _VP, _I64, _VP]),
+    "isycos_search_queries": (_I32, [_VP, _I64, _VP, _VP, _I64, _VP]),
     "isycos_serve_submit": (_I32, [_VP, _I32, _I32, _I64, _I64, ctypes.POINTER(isycos_params),
                                    ctypes.POINTER(_U64)]),
     "isycos_serve_poll": (_I32, [_VP, _U64, _VP, _I64, ctypes.POINTER(_I64),
@@ -302,6 +310,20 @@ def isycos_search_many(ctx, xs, ys, t_begin, t_end, params=None, cap_per_query: 
     n_out = np.zeros(nq, dtype=np.int64)
     _check(ctx, lib().isycos_search_many(ctx, nq, _ptr(xs), _ptr(ys), _ptr(tb), _ptr(te),
                                          ctypes.byref(p), _ptr(out), cap_per_query, _ptr(n_out)))
+    return [out[q * cap_per_query: q * cap_per_query + n_out[q]].copy() for q in range(nq)]
+
+
+def isycos_search_queries(ctx, queries, cap_per_query: int = 4096):
+    """queries: list of (xs, ys, t_begin, t_end, params)."""
+    nq = len(queries)
+    arr = (isycos_query * max(nq, 1))()
+    for i, (a, b, lo, hi, prm) in enumerate(queries):
+        arr[i].xs, arr[i].ys, arr[i].t_begin, arr[i].t_end = a, b, lo, hi
+        arr[i].params = _as_params(prm)
+    out = np.empty(max(nq * cap_per_query, 1), dtype=RESULT_DTYPE)
+    n_out = np.zeros(max(nq, 1), dtype=np.int64)
+    _check(ctx, lib().isycos_search_queries(ctx, nq, ctypes.addressof(arr), _ptr(out),
+                                            cap_per_query, _ptr(n_out)))
     return [out[q * cap_per_query: q * cap_per_query + n_out[q]].copy() for q in range(nq)]
 
 

@@ -132,13 +132,13 @@ inline int batched_grid_need(const BucketTable &T, int nt) {
 constexpr int kSortMax = 4096;
 
 // Sorted path layout in shared memory after the window's m float2 values: the sort keys
-// (8 bytes per slot, the slot count rounded up to a power of two) then the x-ordered records
-// (16 bytes per point).
+// (8 bytes per slot, the slot count rounded up to a power of two), the x-ordered records
+// (16 bytes per point), per-point d_x, d_y and multiplicity (12 bytes), a work counter.
 __host__ __device__ inline size_t sorted_off(int m) { return ((size_t)m * 8 + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t sorted_smem(int m) {
     int n = 1;
     while (n < m) n <<= 1;
-    return sorted_off(m) + (size_t)8 * n + (size_t)16 * m;
+    return sorted_off(m) + (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16;
 }
 
 // Shared memory of a batched launch whose largest window has max_m points; max_sorted is the

@@ -306,52 +306,95 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     __syncthreads();
     bitonic_sort<NT>(ys, N);
 
+    // Phase A: the strip walks.  Lanes take points from a shared counter one at a time, so
+    // that a lane whose walk ends early starts the next point instead of idling while the
+    // rest of its warp walks on.  Per point it leaves d_x, d_y and the multiplicity (or -1
+    // when the k+1-th distance is 0 and the duplicates must be counted in phase B).
+    float *pdx = reinterpret_cast<float *>(scratch + (size_t)8 * N + (size_t)16 * m);
+    float *pdy = pdx + m;
+    int *pcc = reinterpret_cast<int *>(pdy + m);
+    int *ctr = pcc + m;
+    if (threadIdx.x == 0) *ctr = 0;
+    __syncthreads();
+    {
+        int state = 0;   // 0: needs a point, 1: walking, 2: no points left
+        int t = 0, lo = 0, hi = 0;
+        bool alo = false, ahi = false;
+        float xi = 0.0f, yi = 0.0f, xlo = 0.0f, xhi = 0.0f;
+        float bd[K1];
+        int bj[K1];
+        for (;;) {
+            if (state == 0) {
+                t = atomicAdd(ctr, 1);
+                if (t >= m) {
+                    state = 2;
+                } else {
+                    const float4 me = rec[t];
+                    xi = me.x;
+                    yi = me.y;
+#pragma unroll
+                    for (int r = 0; r < K1; ++r) {
+                        bd[r] = kInf;
+                        bj[r] = 0x7fffffff;
+                    }
+                    insert_lex<K1>(bd, bj, 0.0f, __float_as_int(me.z));   // the point itself
+                    lo = t - 1;
+                    hi = t + 1;
+                    alo = lo >= 0;
+                    ahi = hi < m;
+                    if (alo) xlo = rec[lo].x;
+                    if (ahi) xhi = rec[hi].x;
+                    state = 1;
+                }
+            }
+            if (__all_sync(kFull, state == 2)) break;
+            if (state != 1) continue;
+            if (alo || ahi) {
+                const bool take_lo = alo && (!ahi || (xi - xlo) <= (xhi - xi));
+                const float cx = take_lo ? xlo : xhi;
+                const float ax = fabsf(xi - cx);
+                if (ax > bd[K1 - 1]) {            // nothing farther on this side can enter
+                    if (take_lo) alo = false;
+                    else ahi = false;
+                    continue;
+                }
+                const float4 c = rec[take_lo ? lo : hi];
+                const float d = fmaxf(ax, fabsf(yi - c.y));
+                const int jj = __float_as_int(c.z);
+                if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
+                if (take_lo) {
+                    --lo;
+                    alo = lo >= 0;
+                    if (alo) xlo = rec[lo].x;
+                } else {
+                    ++hi;
+                    ahi = hi < m;
+                    if (ahi) xhi = rec[hi].x;
+                }
+            } else {
+                float dxm = 0.0f, dym = 0.0f;
+                int cc = 0;
+#pragma unroll
+                for (int r = 0; r < K1; ++r) {
+                    const float2 v = s[bj[r]];
+                    dxm = fmaxf(dxm, fabsf(xi - v.x));
+                    dym = fmaxf(dym, fabsf(yi - v.y));
+                    cc += bd[r] == 0.0f ? 1 : 0;
+                }
+                pdx[t] = dxm;
+                pdy[t] = dym;
+                pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
+                state = 0;
+            }
+        }
+    }
+    __syncthreads();
+    // Phase B: the marginal counts by binary search, and the duplicate counts left open.
     for (int t = threadIdx.x; t < m; t += NT) {
         const float4 me = rec[t];
         const float xi = me.x, yi = me.y;
         const int ji = __float_as_int(me.z);
-        float bd[K1];
-        int bj[K1];
-#pragma unroll
-        for (int r = 0; r < K1; ++r) {
-            bd[r] = kInf;
-            bj[r] = 0x7fffffff;
-        }
-        insert_lex<K1>(bd, bj, 0.0f, ji);   // the point itself (d = 0)
-        int lo = t - 1, hi = t + 1;
-        float xlo = lo >= 0 ? rec[lo].x : 0.0f, xhi = hi < m ? rec[hi].x : 0.0f;
-        bool alo = lo >= 0, ahi = hi < m;
-        while (alo || ahi) {
-            const bool take_lo = alo && (!ahi || (xi - xlo) <= (xhi - xi));
-            const int u = take_lo ? lo : hi;
-            const float cx = take_lo ? xlo : xhi;
-            const float ax = fabsf(xi - cx);
-            if (ax > bd[K1 - 1]) {            // nothing farther on this side can enter
-                if (take_lo) alo = false;
-                else ahi = false;
-                continue;
-            }
-            const float4 c = rec[u];
-            const float d = fmaxf(ax, fabsf(yi - c.y));
-            const int jj = __float_as_int(c.z);
-            if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
-            if (take_lo) {
-                --lo;
-                alo = lo >= 0;
-                if (alo) xlo = rec[lo].x;
-            } else {
-                ++hi;
-                ahi = hi < m;
-                if (ahi) xhi = rec[hi].x;
-            }
-        }
-        float dxm = 0.0f, dym = 0.0f;
-#pragma unroll
-        for (int r = 0; r < K1; ++r) {
-            const float2 v = s[bj[r]];
-            dxm = fmaxf(dxm, fabsf(xi - v.x));
-            dym = fmaxf(dym, fabsf(yi - v.y));
-        }
+        const float dxm = pdx[t], dym = pdy[t];
         // n_x: the x-sorted range around position t where fabsf(x_i - x) <= d_x
         int l0 = 0, l1 = t;
         while (l0 < l1) {
@@ -387,11 +430,8 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
             else w1 = mid - 1;
         }
         const int cy = w0 - q0 + 1;
-        // multiplicity of (x_i, y_i)
-        int cc = 0;
-#pragma unroll
-        for (int r = 0; r < K1; ++r) cc += bd[r] == 0.0f ? 1 : 0;
-        if (bd[K1 - 1] == 0.0f) {
+        int cc = pcc[t];
+        if (cc < 0) {   // k+1-th distance 0: count the duplicates among the equal x values
             cc = 1;
             for (int u = t - 1; u >= 0 && rec[u].x == xi; --u) cc += rec[u].y == yi ? 1 : 0;
             for (int u = t + 1; u < m && rec[u].x == xi; ++u) cc += rec[u].y == yi ? 1 : 0;

@@ -358,6 +358,10 @@ void isycos_params_default(isycos_params *p) {
     p->pruning = 0;
     p->max_steps = 10000;
     p->seed = 0;
+    p->sel_partitions = 20;
+    p->sel_samples = 6;
+    p->sel_alpha = 0.5;
+    p->sel_rho = 0.5;
 }
 
 isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budget_bytes) {

@@ -42,10 +42,16 @@ isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchPar
     o->t_max_idle = in->t_max_idle >= 0 ? in->t_max_idle : 3;
     o->p = in->p > 0 ? in->p : 3;
     o->mode = in->mode;
-    if (o->mode != 0 && o->mode != 1) return fail(ctx, ISYCOS_E_INVAL, "mode must be 0 (TD) or 1 (BU)");
+    if (o->mode < 0 || o->mode > 2)
+        return fail(ctx, ISYCOS_E_INVAL, "mode must be 0 (TD), 1 (BU) or 2 (selection)");
     o->pruning = in->pruning ? 1 : 0;
     o->max_steps = in->max_steps > 0 ? in->max_steps : 10000;
     o->seed = in->seed;
+    o->sel_partitions = in->sel_partitions > 0 ? in->sel_partitions : 20;
+    o->sel_samples = in->sel_samples > 0 ? in->sel_samples : 6;
+    o->sel_alpha = in->sel_alpha >= 0.0 ? in->sel_alpha : 0.5;
+    o->sel_rho = in->sel_rho > 0.0 ? in->sel_rho : 0.5;
+    if (o->sel_partitions > (1 << 20)) return fail(ctx, ISYCOS_E_INVAL, "sel_partitions too large");
     return ISYCOS_OK;
 }
 
@@ -158,7 +164,7 @@ private:
             }
             if (w.score >= prm.sigma) {
                 found.push_back(isycos_result_window{sc.t, sc.t + s_w_ - 1, w.score, w.mi});
-                ++evals;
+                count(s_w_);
                 sc.t += s_w_;
                 sc.shifted = false;
                 sc.run = 0;
@@ -175,10 +181,11 @@ private:
                     }
                     // Def. 6.2 with w = w_o, w' = w_delta, w'' = the shifted window.
                     noise = (o.score > 0.0) && (e.score < prm.tau) && (w.score < o.score);
-                    evals += 2;
+                    count(mo);
+                    count(d);
                 }
             }
-            ++evals;
+            count(s_w_);
             sc.run = noise ? sc.run + 1 : 0;
             if (sc.run >= prm.p) {
                 sc.t += s_w_;          // Sec. 6.2: skip to just after the current window
@@ -472,7 +479,7 @@ private:
     void begin_climb(const Val &v) {
         Iw_ = v.score;
         mw_ = v.mi;
-        ++evals;
+        count(we_ - ws_ + 1);
         for (double &x : L_) x = Iw_;
         t_idle_ = 0;
         step_ = 0;
@@ -504,7 +511,7 @@ private:
                     return;
                 }
                 const Val &v = g.val[idx];
-                ++evals;
+                count(te - ts + 1);
                 if (!have || v.score > bv.score) {        // first maximum wins
                     have = true;
                     bs = ts;
@@ -526,7 +533,7 @@ private:
                 bool noise = false;
                 if ((int64_t)r * prm.delta_bu >= prm.k + 1) {
                     const Val &e = g.ext_val[s];
-                    ++evals;
+                    count((int64_t)r * prm.delta_bu);
                     // Def. 6.2 with w = current window, w' = extension, w'' = the neighbour.
                     noise = (Iw_ > 0.0) && (e.score < prm.tau) && (pure_sc[s] < Iw_);
                 }
@@ -585,10 +592,152 @@ private:
     int32_t next_chain_ = 0;
 };
 
+// ---------------------------------------------------------------------------------------
+// iSYCOS selection (Sec. 5.3, Algorithm 3)
+// ---------------------------------------------------------------------------------------
+// Sample m of M equal partitions of the range, run SYCOS_TD and SYCOS_BU on each sample
+// (their frontiers batched together), score both with the normalised efficiency scores
+// (Eqs. normalizeruntime, normalizedwindows, normalizedeffscore), where the runtime of a
+// search is the number of pair comparisons m (m - 1) of the windows it scores (a
+// deterministic stand-in for wall-clock time), then run the selected search on the range.
+class SelectMachine : public SearchMachine {
+public:
+    bool want(std::vector<WinReq> &req) override {
+        if (phase_ == 0) {
+            bool any = false;
+            int32_t chain_base = 0;
+            from_.clear();
+            for (size_t i = 0; i < subs_.size(); ++i) {
+                if (sub_done_[i]) continue;
+                std::vector<WinReq> r;
+                if (!subs_[i]->want(r)) {
+                    sub_done_[i] = true;
+                    continue;
+                }
+                int32_t top = 0;
+                for (WinReq &w : r) {
+                    if (w.chain >= 0) {
+                        top = std::max(top, w.chain + 1);
+                        w.chain += chain_base;
+                    }
+                }
+                chain_base += top;
+                from_.push_back({i, r.size()});
+                req.insert(req.end(), r.begin(), r.end());
+                any = true;
+            }
+            if (any) return true;
+            select();
+        }
+        std::vector<WinReq> r;
+        if (!final_->want(r)) {
+            found = final_->found;
+            evals = final_->evals + sub_evals_;
+            cost = final_->cost;
+            return false;
+        }
+        req.insert(req.end(), r.begin(), r.end());
+        return true;
+    }
+
+    void give(const isycos_mi_out *res, size_t n) override {
+        if (phase_ == 0) {
+            size_t off = 0;
+            for (const auto &f : from_) {
+                subs_[f.first]->give(res + off, f.second);
+                off += f.second;
+            }
+            (void)n;
+            return;
+        }
+        final_->give(res, n);
+    }
+
+    void init() {
+        const int64_t N = t_end - t_begin;
+        const int M = prm.sel_partitions;
+        const int ms = std::min(prm.sel_samples, M);
+        const int64_t L = N / M;
+        std::vector<int> idx((size_t)M);
+        for (int i = 0; i < M; ++i) idx[i] = i;
+        for (int i = 0; i < ms; ++i) {   // partial Fisher-Yates shuffle, SplitMix64 draws
+            const uint64_t r = splitmix64_at(prm.seed ^ 0x5E1EC7ULL, (uint64_t)i + 1);
+            const int j = i + (int)(r % (uint64_t)(M - i));
+            std::swap(idx[i], idx[j]);
+        }
+        n_samples_ = ms;
+        if (L > 0) {
+            for (int i = 0; i < ms; ++i) {
+                const int64_t a = t_begin + (int64_t)idx[i] * L;
+                SearchParams p = prm;
+                for (int mode = 0; mode < 2; ++mode) {
+                    p.mode = mode;
+                    subs_.push_back(make_machine(xs, ys, a, a + L, p));
+                }
+            }
+        }
+        sub_done_.assign(subs_.size(), false);
+    }
+
+    int selected = -1;
+    double nscore[2] = {0.0, 0.0};
+
+private:
+    void select() {
+        double t_td = 0.0, t_bu = 0.0, nl_td = 0.0, ns_bu = 0.0;
+        sub_evals_ = 0;
+        for (size_t i = 0; i < subs_.size(); ++i) {
+            const SearchMachine &m = *subs_[i];
+            const bool td = (i % 2) == 0;
+            sub_evals_ += m.evals;
+            (td ? t_td : t_bu) += m.cost;
+            for (const auto &w : m.found) {
+                const bool small = (double)(w.t_e - w.t_s + 1) <= prm.sel_rho * (double)prm.s_max;
+                if (td && !small) nl_td += 1.0;
+                if (!td && small) ns_bu += 1.0;
+            }
+        }
+        if (n_samples_ > 0) {
+            t_td /= (double)n_samples_;
+            t_bu /= (double)n_samples_;
+        }
+        const double tt = t_td + t_bu;
+        const double rt_td = tt > 0.0 ? t_td / tt : 0.5, rt_bu = tt > 0.0 ? t_bu / tt : 0.5;
+        const double nn = ns_bu + nl_td;
+        const double wl_td = nn > 0.0 ? nl_td / nn : 0.0, ws_bu = nn > 0.0 ? ns_bu / nn : 0.0;
+        nscore[0] = prm.sel_alpha * (1.0 / rt_td) + (1.0 - prm.sel_alpha) * wl_td;
+        nscore[1] = prm.sel_alpha * (1.0 / rt_bu) + (1.0 - prm.sel_alpha) * ws_bu;
+        selected = nscore[0] > nscore[1] ? 0 : 1;
+        SearchParams p = prm;
+        p.mode = selected;
+        final_ = make_machine(xs, ys, t_begin, t_end, p);
+        subs_.clear();
+        phase_ = 1;
+    }
+
+    int phase_ = 0;
+    int n_samples_ = 0;
+    int64_t sub_evals_ = 0;
+    std::vector<std::unique_ptr<SearchMachine>> subs_;
+    std::vector<bool> sub_done_;
+    std::vector<std::pair<size_t, size_t>> from_;
+    std::unique_ptr<SearchMachine> final_;
+};
+
 }  // namespace
 
 std::unique_ptr<SearchMachine> make_machine(int32_t xs, int32_t ys, int64_t t_begin, int64_t t_end,
                                             const SearchParams &p) {
+    if (p.mode == 2) {
+        auto m = std::make_unique<SelectMachine>();
+        m->xs = xs;
+        m->ys = ys;
+        m->t_begin = t_begin;
+        m->t_end = t_end;
+        m->prm = p;
+        m->init();
+        return m;
+    }
     if (p.mode == 0) {
         auto m = std::make_unique<TdMachine>();
         m->xs = xs;
@@ -767,30 +916,24 @@ isycos_status isycos_search(isycos_ctx *ctx, int32_t xs, int32_t ys, int64_t t_b
     return isycos_search_many(ctx, 1, &xs, &ys, &t_begin, &t_end, params, out, cap, n_out);
 }
 
-isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs,
-                                 const int32_t *ys, const int64_t *t_begin,
-                                 const int64_t *t_end, const isycos_params *params,
-                                 isycos_result_window *out, int64_t cap_per_query,
-                                 int64_t *n_out) {
-    if (!ctx) return ISYCOS_E_INVAL;
-    if (n_q < 0 || (n_q > 0 && (!xs || !ys || !t_begin || !t_end || !n_out)) || cap_per_query < 0 ||
-        (cap_per_query > 0 && n_q > 0 && !out))
-        return fail(ctx, ISYCOS_E_INVAL, "search: bad arguments");
-    SearchParams p;
-    isycos_status rc = resolve_params(ctx, params, &p);
-    if (rc) return rc;
-    std::lock_guard<std::mutex> g(ctx->engine_mu);
-    cudaSetDevice(ctx->device);
+}  // extern "C"
+
+// Run independent queries (each with its own parameters) to completion.
+static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs, const int32_t *ys,
+                                 const int64_t *t_begin, const int64_t *t_end,
+                                 const SearchParams *prm, size_t prm_stride,
+                                 isycos_result_window *out, int64_t cap_per_query, int64_t *n_out) {
+    isycos_status rc;
     std::vector<std::unique_ptr<SearchMachine>> own;
     std::vector<SearchMachine *> ms;
     for (int64_t q = 0; q < n_q; ++q) {
         if ((rc = check_query(ctx, xs[q], ys[q], t_begin[q], t_end[q]))) return rc;
-        own.push_back(make_machine(xs[q], ys[q], t_begin[q], t_end[q], p));
+        own.push_back(make_machine(xs[q], ys[q], t_begin[q], t_end[q], prm[q * prm_stride]));
         ms.push_back(own.back().get());
     }
     // Independent queries split over engine lanes, one host thread per lane: each thread runs
     // its machines' rounds on its own stream, so that the sequential decision logic of many
-    // queries proceeds in parallel and their small batches overlap on the GPU.
+    // queries proceeds in parallel and their batches overlap on the GPU.
     const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 3) / 4));
     std::vector<Lane *> lanes((size_t)n_lanes);
     for (int i = 0; i < n_lanes; ++i)
@@ -828,6 +971,49 @@ isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
             memcpy(out + q * cap_per_query, f.data(), sizeof(isycos_result_window) * f.size());
     }
     return result;
+}
+
+extern "C" {
+
+isycos_status isycos_search_many(isycos_ctx *ctx, int64_t n_q, const int32_t *xs,
+                                 const int32_t *ys, const int64_t *t_begin,
+                                 const int64_t *t_end, const isycos_params *params,
+                                 isycos_result_window *out, int64_t cap_per_query,
+                                 int64_t *n_out) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_q < 0 || (n_q > 0 && (!xs || !ys || !t_begin || !t_end || !n_out)) || cap_per_query < 0 ||
+        (cap_per_query > 0 && n_q > 0 && !out))
+        return fail(ctx, ISYCOS_E_INVAL, "search: bad arguments");
+    SearchParams p;
+    isycos_status rc = resolve_params(ctx, params, &p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    return run_queries(ctx, n_q, xs, ys, t_begin, t_end, &p, 0, out, cap_per_query, n_out);
+}
+
+isycos_status isycos_search_queries(isycos_ctx *ctx, int64_t n_q, const isycos_query *queries,
+                                    isycos_result_window *out, int64_t cap_per_query,
+                                    int64_t *n_out) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (n_q < 0 || (n_q > 0 && (!queries || !n_out)) || cap_per_query < 0 ||
+        (cap_per_query > 0 && n_q > 0 && !out))
+        return fail(ctx, ISYCOS_E_INVAL, "search: bad arguments");
+    std::vector<SearchParams> prm((size_t)n_q);
+    std::vector<int32_t> xs((size_t)n_q), ys((size_t)n_q);
+    std::vector<int64_t> tb((size_t)n_q), te((size_t)n_q);
+    for (int64_t q = 0; q < n_q; ++q) {
+        isycos_status rc = resolve_params(ctx, &queries[q].params, &prm[q]);
+        if (rc) return rc;
+        xs[q] = queries[q].xs;
+        ys[q] = queries[q].ys;
+        tb[q] = queries[q].t_begin;
+        te[q] = queries[q].t_end;
+    }
+    std::lock_guard<std::mutex> g(ctx->engine_mu);
+    cudaSetDevice(ctx->device);
+    return run_queries(ctx, n_q, xs.data(), ys.data(), tb.data(), te.data(), prm.data(), 1, out,
+                       cap_per_query, n_out);
 }
 
 }  // extern "C"

@@ -21,6 +21,8 @@ struct SearchParams {
     int delta_bu;
     int h, t_max_idle, p, mode, pruning, max_steps;
     uint64_t seed;
+    int sel_partitions, sel_samples;   // Algorithm 3
+    double sel_alpha, sel_rho;
 };
 
 isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchParams *out);
@@ -46,8 +48,13 @@ public:
     SearchParams prm{};
     std::vector<isycos_result_window> found;
     int64_t evals = 0;       // window scores consumed by the decisions
+    double cost = 0.0;       // their pair comparisons, sum m (m - 1): the search's "runtime"
 
 protected:
+    void count(int64_t m) {
+        ++evals;
+        cost += (double)m * (double)(m - 1);
+    }
     double score_of(const isycos_mi_out &r) const { return prm.score_kind == 1 ? r.mi : r.nmi; }
     static uint64_t key(int64_t start, int32_t m) { return ((uint64_t)start << 15) | (uint64_t)m; }
     struct Val {

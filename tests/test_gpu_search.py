@@ -273,3 +273,39 @@ def test_decided_windows_equal_the_oracles_evaluations(ctx, mode):
     _, n_evals = (O.search_td if mode == 0 else O.search_bu)(x, y, **kw)
     assert st["decided_windows"] == n_evals
     assert st["windows"] >= n_evals
+
+
+def test_search_queries_mixed_modes_equal_single_searches(ctx):
+    api = _api()
+    ids = []
+    for p in range(3):
+        x, y, _ = synth.planted_pair(2, 10 + p, 6000, len_lo=50, len_hi=800)
+        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    queries = []
+    for i, (a, b) in enumerate(ids):
+        queries.append((a, b, 0, 6000, dict(k=4, s_min=32, s_max=512, mode=0, pruning=i % 2)))
+        queries.append((a, b, 500, 5500, dict(k=3, s_min=40, s_max=300, mode=1, pruning=1, seed=i)))
+    got = api.isycos_search_queries(ctx, queries)
+    for q, g in zip(queries, got):
+        assert np.array_equal(api.isycos_search(ctx, *q), g)
+
+
+@pytest.mark.parametrize("case", ["planted", "weak"])
+def test_selection_matches_oracle(ctx, case):
+    """iSYCOS selection (Algorithm 3): the GPU search samples the same partitions, scores TD
+    and BU with the same deterministic runtime, selects the same search and returns its
+    windows; its decided-window count equals the oracle's."""
+    api = _api()
+    if case == "planted":
+        x, y = synth.planted_small_pair()
+    else:
+        x, y, _ = synth.planted_pair(3, 1, 4000, coverage=0.1, len_lo=40, len_hi=200)
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, pruning=1, seed=17)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    api.isycos_reset_stats(ctx)
+    got = api.isycos_search(ctx, xs, ys, 0, len(x), dict(kw, mode=2, sel_partitions=8,
+                                                          sel_samples=3))
+    st = api.isycos_get_stats(ctx)
+    ref, n, sel, _ = O.search_auto(x, y, partitions=8, samples=3, **kw)
+    _same(got, ref)
+    assert st["decided_windows"] == n

@@ -99,3 +99,27 @@ def test_invalid_params():
         O.search_td(x, y, k=4, s_min=4, s_max=64)       # s_min < k + 1
     with pytest.raises(ValueError):
         O.search_bu(x, y, k=4, s_min=64, s_max=32)      # s_max < s_min
+
+
+def test_selection_scores_follow_the_equations():
+    # Eqs. normalizeruntime / normalizedwindows / normalizedeffscore (Sec. 5.3) by hand:
+    # t_TD = 100, t_BU = 300 -> t~ = 0.25, 0.75; nL_TD = 5, nS_BU = 2 -> n~ = 5/7, 2/7
+    td, bu = O.nscores(100.0, 300.0, 5.0, 2.0, alpha=0.5)
+    assert td == pytest.approx(0.5 * 4.0 + 0.5 * 5.0 / 7.0)
+    assert bu == pytest.approx(0.5 / 0.75 + 0.5 * 2.0 / 7.0)
+    # alpha = 1: runtime only; alpha = 0: window counts only
+    assert O.nscores(1.0, 3.0, 0.0, 9.0, alpha=1.0) == pytest.approx((4.0, 4.0 / 3.0))
+    assert O.nscores(1.0, 3.0, 1.0, 3.0, alpha=0.0) == pytest.approx((0.25, 0.75))
+    # degenerate: nothing evaluated, nothing found
+    assert O.nscores(0.0, 0.0, 0.0, 0.0, alpha=0.5) == pytest.approx((1.0, 1.0))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_selection_runs_the_selected_search(seed):
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, pruning=1, seed=seed)
+    wins, n, sel, sc = O.search_auto(x, y, partitions=10, samples=4, **kw)
+    assert sel == (0 if sc[0] > sc[1] else 1)
+    ref, _ = (O.search_td if sel == 0 else O.search_bu)(x, y, **kw)
+    assert [(a, b) for a, b, _, _ in wins] == [(a, b) for a, b, _, _ in ref]
+    assert n > 0
