@@ -51,6 +51,8 @@ typedef int32_t isycos_status;
 #define ISYCOS_MAX_M 16384
 /* Largest number of neighbours k. */
 #define ISYCOS_MAX_K 8
+/* Largest LAHC idle limit T_maxIdle of SYCOS_BU (its rings reach N_{T_maxIdle + 1}). */
+#define ISYCOS_MAX_IDLE 64
 
 typedef struct isycos_ctx isycos_ctx;
 
@@ -95,7 +97,7 @@ typedef struct {
     int32_t delta_td;    /* TD sliding step; <= 0: max(k + 1, s_w / 4) per layer         */
     int32_t delta_bu;    /* BU moving step; <= 0: max(1, s_min / 4)                      */
     int32_t h;           /* LAHC history length; <= 0: 8                                 */
-    int32_t t_max_idle;  /* LAHC idle limit; < 0: 3                                      */
+    int32_t t_max_idle;  /* LAHC idle limit; < 0: 3; > ISYCOS_MAX_IDLE: ISYCOS_E_INVAL    */
     int32_t p;           /* consecutive noise detections before pruning; <= 0: 3         */
     int32_t mode;        /* 0: SYCOS_TD, 1: SYCOS_BU, 2: iSYCOS selection (Alg. 3)       */
     int32_t pruning;     /* 0 off, 1 noise pruning (Sec. 6) on                           */
@@ -133,7 +135,11 @@ typedef struct {
                                their [start, stop] intervals (CUDA events on each
                                launching stream; concurrent launches counted once)    */
     int64_t mi_kernel_launches; /* launches timed in mi_kernel_ms                      */
-} isycos_stats;
+    /* Per size bucket b = 0 .. 14 (windows with 2^(b-1) < m <= 2^b; b = 0: m = 1):      */
+    int64_t windows_by_size[15];   /* batched windows evaluated                          */
+    int64_t launches_by_size[15];  /* batched launches whose largest window is in b       */
+    double launch_ms_by_size[15];  /* their event-timed durations, summed (not a union)   */
+} isycos_stats;   /* 440 bytes */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes caps the device memory the
  * context may hold for series and work buffers (0: 90% of the free memory at creation).

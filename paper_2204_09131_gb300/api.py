@@ -76,7 +76,9 @@ class isycos_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("incr_windows", ctypes.c_int64), ("incr_full_points", ctypes.c_int64),
                 ("queries_done", ctypes.c_int64), ("decided_windows", ctypes.c_int64),
-                ("mi_kernel_ms", ctypes.c_double), ("mi_kernel_launches", ctypes.c_int64)]
+                ("mi_kernel_ms", ctypes.c_double), ("mi_kernel_launches", ctypes.c_int64),
+                ("windows_by_size", ctypes.c_int64 * 15), ("launches_by_size", ctypes.c_int64 * 15),
+                ("launch_ms_by_size", ctypes.c_double * 15)]
 
 
 # NumPy views of the C structs (same layout).
@@ -354,7 +356,11 @@ def isycos_serve_cancel(ctx, ticket: int):
 def isycos_get_stats(ctx) -> dict:
     s = isycos_stats()
     _check(ctx, lib().isycos_get_stats(ctx, ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in isycos_stats._fields_}
+    out = {}
+    for f, _ in isycos_stats._fields_:
+        v = getattr(s, f)
+        out[f] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def isycos_reset_stats(ctx):

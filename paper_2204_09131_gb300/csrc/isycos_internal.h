@@ -44,7 +44,8 @@ struct BucketTable {
 struct BatchArgs {
     const WorkItem *items;
     const BucketTable *table;
-    int32_t *queue;              // two work counters, CTA jobs and warp items (zeroed)
+    int32_t *queue;              // CTA jobs, warp items, CTAs finished: zero at launch; the
+                                 // last CTA to finish zeroes them again
     const long long *psi_fx;
     const long long *log_fx;
     isycos_mi_out *out;

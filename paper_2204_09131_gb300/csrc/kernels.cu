@@ -535,6 +535,18 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         ll = warp_sum64(ll);
         if (lane == 0) write_result(a.out + it.out, a.k, it.m, lp, ll, a.psi_fx, a.log_fx);
     }
+    // The last CTA to finish zeroes the work counters for the next launch on this buffer:
+    // every other CTA has taken its last job before it counts itself out.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.queue + 2, 1) == (int)gridDim.x - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+            a.queue[2] = 0;
+            __threadfence();
+        }
+    }
 }
 
 // Plain form: one window per launch; CTA b handles the blocks b*W .. b*W + W - 1 and the

@@ -90,7 +90,7 @@ __global__ void noalloc_classify(NoallocPrep a) {
     const bool ok = m >= a.k + 1 && m <= a.max_m && s >= 0 && s + m <= a.n;
     if (!ok) {
         ctl_slot(a.scratch)[i] = -1;
-        atomicOr(ctl_counts(a.scratch) + kBuckets + 2, 1);
+        atomicOr(ctl_counts(a.scratch) + kBuckets + 3, 1);
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         a.out[i].mi = nan;
         a.out[i].h_w = nan;
@@ -206,7 +206,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     pa.nt = nt;
     pa.scratch = d.scratch;
     pa.out = d_out;
-    // bucket counters, the two work counters and the error flag start at zero on every call
+    // bucket counters, the three work counters and the error flag start at zero on every call
     if (cudaMemsetAsync(d.scratch, 0, 128, st) != cudaSuccess) return ISYCOS_E_CUDA;
     const int blocks = (int)((n_w + 255) / 256);
     noalloc_classify<<<blocks, 256, 0, st>>>(pa);

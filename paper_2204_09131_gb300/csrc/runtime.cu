@@ -73,9 +73,16 @@ isycos_status host_reserve(isycos_ctx *ctx, HostBuf &b, size_t bytes) {
     size_t want = std::max(bytes, b.cap + b.cap / 2);
     if (b.p) cudaFreeHost(b.p);
     b.p = nullptr;
+    b.dev = nullptr;
     b.cap = 0;
-    cudaError_t e = cudaMallocHost(&b.p, want);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost");
+    cudaError_t e = cudaHostAlloc(&b.p, want, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaHostAlloc");
+    e = cudaHostGetDevicePointer(&b.dev, b.p, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(b.p);
+        b.p = nullptr;
+        return cuda_fail(ctx, e, "cudaHostGetDevicePointer");
+    }
     b.cap = want;
     return ISYCOS_OK;
 }
@@ -201,16 +208,19 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     }
 
     if ((rc = dev_reserve(ctx, L.d_items, stage_bytes))) return rc;
+    if (!L.d_queue.p) L.queue_clean = false;
     if ((rc = dev_reserve(ctx, L.d_queue, 256))) return rc;
-    if ((rc = dev_reserve(ctx, L.d_out, sizeof(isycos_mi_out) * n))) return rc;
     if (nx) {
         if ((rc = dev_reserve(ctx, L.d_nx, 4 * total_pts))) return rc;
         if ((rc = dev_reserve(ctx, L.d_ny, 4 * total_pts))) return rc;
         if ((rc = dev_reserve(ctx, L.d_c, 4 * total_pts))) return rc;
     }
-    cudaError_t e = cudaMemcpyAsync(L.d_items.p, stage, stage_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.d_queue.p, 0, 8, st);
+    // The work counters are zeroed once; every launch leaves them at zero.
+    cudaError_t e = cudaSuccess;
+    if (!L.queue_clean) e = cudaMemsetAsync(L.d_queue.p, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_items.p, stage, stage_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "staging the window list");
+    L.queue_clean = true;
 
     int grid;
     if ((rc = launch_grid(ctx, k, nt, smem, batched_grid_need(T, nt), &grid))) return rc;
@@ -220,7 +230,9 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     a.queue = reinterpret_cast<int32_t *>(L.d_queue.p);
     a.psi_fx = ctx->d_psi_fx;
     a.log_fx = ctx->d_log_fx;
-    a.out = reinterpret_cast<isycos_mi_out *>(L.d_out.p);
+    // results go straight to the pinned, mapped host buffer (no copy back)
+    isycos_mi_out *h_out = reinterpret_cast<isycos_mi_out *>(L.h_table.p);
+    a.out = reinterpret_cast<isycos_mi_out *>(L.h_table.dev);
     a.nx = nx ? reinterpret_cast<int32_t *>(L.d_nx.p) : nullptr;
     a.ny = nx ? reinterpret_cast<int32_t *>(L.d_ny.p) : nullptr;
     a.c = nx ? reinterpret_cast<int32_t *>(L.d_c.p) : nullptr;
@@ -230,10 +242,11 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
-    isycos_mi_out *h_out = reinterpret_cast<isycos_mi_out *>(L.h_table.p);
-    e = cudaMemcpyAsync(h_out, L.d_out.p, sizeof(isycos_mi_out) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && nx) {
+    if (e != cudaSuccess) {
+        L.queue_clean = false;
+        return cuda_fail(ctx, e, "MI kernel launch");
+    }
+    if (nx) {
         e = cudaMemcpyAsync(nx, L.d_nx.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ny, L.d_ny.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c, L.d_c.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
@@ -242,7 +255,10 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     float t0 = 0.0f, t1 = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ctx->ev_ref, L.ev_start);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev_ref, L.ev_stop);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel");
+    if (e != cudaSuccess) {
+        L.queue_clean = false;
+        return cuda_fail(ctx, e, "MI kernel");
+    }
     memcpy(out, h_out, sizeof(isycos_mi_out) * n);
     add_stats(ctx, n, pairs, 1, 1, 0);
     {
@@ -251,6 +267,10 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
         std::lock_guard<std::mutex> g(ctx->stats_mu);
         ctx->kernel_iv.push_back({t0, t1});
         ctx->stats.mi_kernel_launches += 1;
+        for (int q = 0; q < kBuckets; ++q) ctx->stats.windows_by_size[kBuckets - 1 - q] += count[q];
+        const int bmax = kBuckets - 1 - bucket_slot(max_m);
+        ctx->stats.launches_by_size[bmax] += 1;
+        ctx->stats.launch_ms_by_size[bmax] += (double)(t1 - t0);
     }
     return ISYCOS_OK;
 }
@@ -623,7 +643,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     pa.status = reinterpret_cast<int32_t *>(ctx->d_status.p);
     pa.out = d_out;
     cudaError_t e = cudaMemsetAsync(ctx->d_bcount.p, 0, 4 * kBuckets, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_dev_queue.p, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_dev_queue.p, 0, 16, st);
     int launches = 0;
     if (e == cudaSuccess) e = launch_prep(pa, st, &launches);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "window preparation");

@@ -27,7 +27,8 @@ struct DevBuf {
 
 // A growable pinned host buffer.
 struct HostBuf {
-    void *p = nullptr;
+    void *p = nullptr;     // pinned and mapped
+    void *dev = nullptr;   // its device address
     size_t cap = 0;
 };
 
@@ -39,6 +40,7 @@ struct Lane {
     DevBuf d_items, d_queue, d_out, d_nx, d_ny, d_c;
     DevBuf d_chain_desc, d_chain_steps, d_chain_state, d_chain_recomp, d_chain_out;
     HostBuf h_items, h_table;          // pinned staging: table + items; results
+    bool queue_clean = false;          // d_queue holds zeroed work counters
     std::vector<int32_t> h_slot;       // per-call bucket slots (reused)
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
 };

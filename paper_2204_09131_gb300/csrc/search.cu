@@ -40,6 +40,8 @@ isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchPar
     o->delta_bu = in->delta_bu > 0 ? in->delta_bu : std::max(1, o->s_min / 4);
     o->h = in->h > 0 ? in->h : 8;
     o->t_max_idle = in->t_max_idle >= 0 ? in->t_max_idle : 3;
+    if (o->t_max_idle > kMaxIdle)
+        return fail(ctx, ISYCOS_E_INVAL, "t_max_idle = %d > %d", o->t_max_idle, kMaxIdle);
     o->p = in->p > 0 ? in->p : 3;
     o->mode = in->mode;
     if (o->mode < 0 || o->mode > 2)
@@ -238,6 +240,7 @@ public:
                 we_ = c_ + prm.s_min - 1;
                 invalidate_rings();
                 grid_.reset(ws_, we_, prm.delta_bu);
+                grid_.follow(ws_, we_, prm.t_max_idle + 2);
                 // a climb always evaluates ring N_1 of its first window next: ask it now
                 if (!lookup(ws_, (int32_t)(we_ - ws_ + 1), &start_val_))
                     ask(ws_, we_, kDestStart, -1, false);
@@ -262,6 +265,7 @@ public:
                 // climb moves by one delta and the remaining rings when it does not.
                 r_last = std::max(r_last, std::min(prm.t_max_idle + 1, spec_depth()));
                 const size_t before = asked_.size();
+                grid_.follow(ws_, we_, prm.t_max_idle + 2);   // every ring of this centre
                 ask_ring(r, dropped_[0], dropped_[1]);
                 // speculate only when this step needs a round trip anyway
                 if (asked_.size() > before)
@@ -292,9 +296,8 @@ public:
                 start_val_ = v;
                 cache_.put(key(d.ts, (int32_t)(d.te - d.ts + 1)), v);
             } else if (d.kind == kDestCell) {
-                rings_[d.r].val[d.idx] = v;
-                rings_[d.r].have[d.idx] = 1;
-                grid_.put(d.ts, d.te, v);
+                grid_.val[(size_t)d.idx] = v;   // the cell index taken when it was asked
+                grid_.tag[(size_t)d.idx] = grid_.gen;
             } else if (d.kind == kDestExt) {
                 rings_[d.r].ext_val[d.idx] = v;
                 rings_[d.r].ext_have[d.idx] = 1;
@@ -308,6 +311,7 @@ public:
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
         rings_.resize((size_t)prm.t_max_idle + 2);
+        grid_.init(2 * (prm.t_max_idle + 2) + 2);
     }
 
 private:
@@ -320,12 +324,17 @@ private:
     // Scores of this climb's windows on its delta grid: window [c + a d, c + s_min - 1 + b d]
     // at cell (a, b) of a square array that follows the current window.
     struct GridCache {
-        static constexpr int G = 64;
+        int G = 64;
         int64_t bs = 0, be = 0, d = 1;
         int64_t a0 = 0, b0 = 0;   // offsets of cell (0, 0)
         uint32_t gen = 1;
-        std::vector<Val> val = std::vector<Val>((size_t)G * G);
-        std::vector<uint32_t> tag = std::vector<uint32_t>((size_t)G * G, 0);
+        std::vector<Val> val;
+        std::vector<uint32_t> tag;
+        void init(int min_side) {
+            G = std::max(64, min_side);
+            val.assign((size_t)G * G, Val{0.0, 0.0});
+            tag.assign((size_t)G * G, 0);
+        }
         void reset(int64_t s, int64_t e, int64_t delta) {
             bs = s;
             be = e;
@@ -353,6 +362,15 @@ private:
             val[i] = v;
             tag[i] = gen;
         }
+        // Cell of offset (a, b) from the window (ws, we), which lies on the grid and whose
+        // square of half-side max(|a|, |b|) + 1 is inside the array (after follow()).
+        size_t near(int64_t ac, int64_t bc, int a, int b) const {
+            return (size_t)(ac + a - a0) * G + (size_t)(bc + b - b0);
+        }
+        void centre(int64_t ws, int64_t we, int64_t *ac, int64_t *bc) const {
+            *ac = (ws - bs) / d;
+            *bc = (we - be) / d;
+        }
         // keep the square of half-side R around the window (ws, we) inside the array
         void follow(int64_t ws, int64_t we, int R) {
             const int64_t ac = (ws - bs) / d, bc = (we - be) / d;
@@ -375,12 +393,11 @@ private:
             b0 = nb0;
         }
     };
-    // Results for ring N_r around the centre (cs, ce): a cell per offset (a, b).
+    // Ring N_r asked around the centre (cs, ce).  Its windows' scores are cells of the grid
+    // cache; the noise-test extension windows are kept here.
     struct Ring {
         bool asked = false;
         int64_t cs = 0, ce = -1;
-        std::vector<Val> val;
-        std::vector<char> have;
         Val ext_val[2];
         char ext_have[2] = {0, 0};
     };
@@ -418,28 +435,21 @@ private:
     // from (-r, -r) so that consecutive windows differ by one delta at one end (the current
     // window starts the chain), then the noise-test extension windows.
     void ask_ring(int r, bool drop_left, bool drop_right) {
-        grid_.follow(ws_, we_, r + 1);
         Ring &g = rings_[r];
-        const int side = 2 * r + 1;
         g.asked = true;
         g.cs = ws_;
         g.ce = we_;
-        g.val.assign((size_t)side * side, Val{0.0, 0.0});
-        g.have.assign((size_t)side * side, 0);
         g.ext_have[0] = g.ext_have[1] = 0;
         const int32_t chain = next_chain_++;
         const size_t first = asked_.size();
+        int64_t ac, bc;
+        grid_.centre(ws_, we_, &ac, &bc);
         auto visit = [&](int a, int b) {
             int64_t ts, te;
             if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
-            const int idx = (a + r) * side + (b + r);
-            Val v;
-            if (grid_.get(ts, te, &v)) {   // evaluated earlier in this climb
-                g.val[idx] = v;
-                g.have[idx] = 1;
-                return;
-            }
-            ask(ts, te, kDestCell, r, false, idx, chain);
+            const size_t ci = grid_.near(ac, bc, a, b);
+            if (grid_.tag[ci] == grid_.gen) return;   // evaluated earlier in this climb
+            ask(ts, te, kDestCell, r, false, (int)ci, chain);
         };
         for (int b = -r; b <= r; ++b) visit(-r, b);
         for (int a = -r + 1; a <= r; ++a) visit(a, r);
@@ -494,23 +504,27 @@ private:
     // One LAHC step on ring N_r (Algorithm 2), with the current dropped directions.
     void decide(int r) {
         const Ring &g = rings_[r];
-        const int side = 2 * r + 1;
+        int64_t ac, bc;
+        grid_.centre(ws_, we_, &ac, &bc);
         bool have = false;
         int64_t bs = 0, be = 0;
         Val bv{0.0, 0.0};
         double pure_sc[2] = {0.0, 0.0};
         bool pure_found[2] = {false, false};
         for (int64_t a = -r; a <= r; ++a)
-            for (int64_t b = -r; b <= r; ++b) {
+            // the perimeter of the square, b ascending within each a
+            for (int64_t b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
                 int64_t ts, te;
                 if (!keep(a, b, r, dropped_[0], dropped_[1], &ts, &te)) continue;
-                const size_t idx = (size_t)(a + r) * side + (b + r);
-                if (!g.have[idx]) {   // cannot happen: asked with fewer directions dropped
+                const size_t ci = grid_.near(ac, bc, (int)a, (int)b);
+                if (grid_.tag[ci] != grid_.gen) {
+                    // only when the cache moved away from this centre since the ring was
+                    // asked: ask it again
                     phase_ = kRing;
                     rings_[r].asked = false;
                     return;
                 }
-                const Val &v = g.val[idx];
+                const Val &v = grid_.val[ci];
                 count(te - ts + 1);
                 if (!have || v.score > bv.score) {        // first maximum wins
                     have = true;

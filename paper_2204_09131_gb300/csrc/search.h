@@ -11,6 +11,8 @@
 
 namespace isy {
 
+constexpr int kMaxIdle = ISYCOS_MAX_IDLE;   // largest LAHC idle limit (rings up to N_{T+1})
+
 // Parameters after defaults are resolved.
 struct SearchParams {
     int k;
