@@ -107,7 +107,13 @@ typedef struct {
     int32_t sel_samples;    /* Alg. 3: m partitions sampled; <= 0: 6                       */
     double sel_alpha;       /* Alg. 3: weight of the runtime factor; < 0: 0.5               */
     double sel_rho;         /* Alg. 3: a window is small iff size <= rho * s_max; <= 0: 0.5 */
-} isycos_params;
+    int32_t chunks;         /* Alg. 4: n_p overlapping chunks searched independently
+                               (chunk i = [i L - s_max, (i + 1) L) of the range, L = floor(
+                               length / n_p), clipped); their windows concatenated and
+                               sorted by t_s, so windows of different chunks may overlap;
+                               <= 1: one search over the whole range                    */
+    int32_t estimator;      /* 0: Kraskov estimator 2 (default); 1: Kraskov estimator 1    */
+} isycos_params;   /* 104 bytes */
 
 /* One correlated window found by a search.  32 bytes. */
 typedef struct {
@@ -297,8 +303,14 @@ isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int
 #define ISYCOS_OPT_INCREMENTAL 2   /* searches: 0 off, 1 auto (default), 2 always           */
 #define ISYCOS_OPT_SERVE_SLOTS 3   /* serving: most queries admitted at once (default 64)   */
 #define ISYCOS_OPT_SERVE_QUEUE 4   /* serving: most queries waiting (default 100000)        */
-#define ISYCOS_OPT_LANES 5         /* searches: most engine lanes (host thread + stream)
-                                      (default: half the host cores, at most 8)              */
+#define ISYCOS_OPT_LANES 5         /* searches: most engine lanes (host thread + stream +
+                                      work buffers), 1 .. 16 (default: half the host cores,
+                                      at most 8)                                             */
+#define ISYCOS_OPT_ESTIMATOR 6     /* estimator of isycos_mi_windows, _points, _device and
+                                      _plain: 0 Kraskov's second (Eq. KSGmi, default), 1
+                                      Kraskov's first, psi(k) + psi(m) - <psi(n_x + 1) +
+                                      psi(n_y + 1)> with strict counts in strips of half-width
+                                      eps_i (searches take isycos_params.estimator)          */
 isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
 
 /* Window MI that allocates nothing.  The paper has no counterpart: this entry point

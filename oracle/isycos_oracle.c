@@ -9,7 +9,9 @@
  *     with the counting rule of the box-assisted example in Sec. 7.1;
  *   - the normalised score I_w / H_w of Sec. 5.4 (Eq. normalizedMI);
  *   - SYCOS_TD (Sec. 5.1, Algorithm 1) and SYCOS_BU (Sec. 5.2, Algorithm 2) with the
- *     MI-based noise pruning of Sec. 6 (Def. 6.2; Secs. 6.2 and 6.3).
+ *     MI-based noise pruning of Sec. 6 (Def. 6.2; Secs. 6.2 and 6.3);
+ *   - the iSYCOS selection between them (Sec. 5.3, Algorithm 3) and the chunked search
+ *     of the distributed iSYCOS (Sec. 7.3, Algorithm 4).
  *
  * Only the tests, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
  * leg may load or call this file.  It shares no code, header, table or constant
@@ -152,12 +154,16 @@ static int orc_before(float d1, int64_t j1, float d2, int64_t j2)
 }
 
 /* Counts for one point i of the window {(x_j, y_j)}, j = 0 .. m-1.
- * nx, ny: marginal counts (j != i, inclusive); c: multiplicity of (x_i, y_i) (includes i);
- * eps: k-th neighbour distance; dxm, dym: per-dimension neighbour distances. */
-int orc_ksg_point(const float *x, const float *y, int64_t m, int32_t k, int64_t i,
-                  int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm, float *dym)
+ * Estimator 0 (Kraskov's second, Eq. KSGmi): nx, ny = marginal counts (j != i, inclusive)
+ * within the per-dimension neighbour distances dxm, dym.
+ * Estimator 1 (Kraskov's first): nx, ny = #{j != i : |x_i - x_j| < eps} (strict), the
+ * marginal strips both of half-width eps (reported in dxm, dym).
+ * c: multiplicity of (x_i, y_i) (includes i); eps: k-th neighbour distance. */
+int orc_ksg_point_est(const float *x, const float *y, int64_t m, int32_t k, int32_t est,
+                      int64_t i, int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm,
+                      float *dym)
 {
-    if (k < 1 || m < (int64_t)k + 1 || i < 0 || i >= m) return ORC_EINVAL;
+    if (k < 1 || m < (int64_t)k + 1 || i < 0 || i >= m || (est != 0 && est != 1)) return ORC_EINVAL;
     float *bd = (float *)malloc(sizeof(float) * (size_t)k);
     int64_t *bj = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
     if (!bd || !bj) { free(bd); free(bj); return ORC_ENOMEM; }
@@ -189,7 +195,20 @@ int orc_ksg_point(const float *x, const float *y, int64_t m, int32_t k, int64_t 
 
     /* Marginal counts: points inside the marginal strips (inclusive), self excluded. */
     int32_t cx = 0, cy = 0, cc = 0;
-    for (int64_t j = 0; j < m; ++j) {
+    if (est == 1) {
+        /* Kraskov's first estimator: strips of half-width eps = d to the k-th neighbour,
+         * points strictly inside counted. */
+        float e = bd[k - 1];
+        for (int64_t j = 0; j < m; ++j) {
+            if (x[j] == x[i] && y[j] == y[i]) ++cc;
+            if (j == i) continue;
+            if (fabsf(x[i] - x[j]) < e) ++cx;
+            if (fabsf(y[i] - y[j]) < e) ++cy;
+        }
+        dx = e;
+        dy = e;
+    }
+    for (int64_t j = 0; j < m && est == 0; ++j) {
         float ax = fabsf(x[i] - x[j]);
         float ay = fabsf(y[i] - y[j]);
         if (g_mutation == ORC_MUT_SWAP_NY) ay = ax;
@@ -215,19 +234,28 @@ int orc_ksg_point(const float *x, const float *y, int64_t m, int32_t k, int64_t 
     return ORC_OK;
 }
 
-/* Eq. KSGmi on the window {(x_j, y_j)}, j = 0 .. m-1.  Per-point arrays may be NULL. */
-int orc_ksg_window(const float *x, const float *y, int64_t m, int32_t k,
-                   int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm, float *dym,
-                   orc_mi *out)
+int orc_ksg_point(const float *x, const float *y, int64_t m, int32_t k, int64_t i,
+                  int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm, float *dym)
+{
+    return orc_ksg_point_est(x, y, m, k, 0, i, nx, ny, c, eps, dxm, dym);
+}
+
+/* MI of the window {(x_j, y_j)}, j = 0 .. m-1.  Estimator 0 is Eq. KSGmi (Kraskov's second
+ * estimator); estimator 1 is Kraskov's first, psi(k) + psi(m) - <psi(n_x + 1) + psi(n_y + 1)>.
+ * Per-point arrays may be NULL. */
+int orc_ksg_window_est(const float *x, const float *y, int64_t m, int32_t k, int32_t est,
+                       int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm, float *dym,
+                       orc_mi *out)
 {
     if (k < 1 || m < (int64_t)k + 1 || m > ORC_TABLE_MAX - 1 || out == NULL) return ORC_EINVAL;
+    if (est != 0 && est != 1) return ORC_EINVAL;
     if (!orc_tables_ready()) return ORC_ENOMEM;
     int64_t s_psi = 0, s_log = 0;
     double sum_psi = 0.0, sum_log = 0.0;
     for (int64_t i = 0; i < m; ++i) {
         int32_t a, b, cc;
         float e, u, v;
-        int rc = orc_ksg_point(x, y, m, k, i, &a, &b, &cc, &e, &u, &v);
+        int rc = orc_ksg_point_est(x, y, m, k, est, i, &a, &b, &cc, &e, &u, &v);
         if (rc != ORC_OK) return rc;
         if (nx) nx[i] = a;
         if (ny) ny[i] = b;
@@ -236,17 +264,18 @@ int orc_ksg_window(const float *x, const float *y, int64_t m, int32_t k,
         if (dxm) dxm[i] = u;
         if (dym) dym[i] = v;
         int32_t ia = a, ib = b;
-        if (g_mutation == ORC_MUT_PSI_PLUS_ONE) { ia += 1; ib += 1; }
+        if (est == 1 || g_mutation == ORC_MUT_PSI_PLUS_ONE) { ia += 1; ib += 1; }
         s_psi += g_psi_fx[ia] + g_psi_fx[ib];
         s_log += g_log_fx[cc];
         sum_psi += g_psi[ia] + g_psi[ib];
         sum_log += log((double)cc);
     }
-    double inv_k = (g_mutation == ORC_MUT_DROP_INV_K) ? 0.0 : 1.0 / (double)k;
+    double inv_k = (est == 1 || g_mutation == ORC_MUT_DROP_INV_K) ? 0.0 : 1.0 / (double)k;
     int64_t mm = (g_mutation == ORC_MUT_PSI_M_MINUS) ? m - 1 : m;
     double md = (double)m;
 
-    /* Canonical evaluation order: ((psi(k) - 1/k) + psi(m)) - S_psi / m. */
+    /* Canonical evaluation order: ((psi(k) - 1/k) + psi(m)) - S_psi / m (estimator 1: the
+     * same with 1/k = 0, which leaves psi(k) unchanged). */
     double psi_k = ldexp((double)g_psi_fx[k], -32);
     double psi_m = ldexp((double)g_psi_fx[mm], -32);
     double mean_psi = ldexp((double)s_psi, -32) / md;
@@ -263,6 +292,13 @@ int orc_ksg_window(const float *x, const float *y, int64_t m, int32_t k,
     out->h_exact = log(md) - sum_log / md;
     if (g_mutation == ORC_MUT_H_SIGN) out->h_exact = -out->h_exact;
     return ORC_OK;
+}
+
+int orc_ksg_window(const float *x, const float *y, int64_t m, int32_t k,
+                   int32_t *nx, int32_t *ny, int32_t *c, float *eps, float *dxm, float *dym,
+                   orc_mi *out)
+{
+    return orc_ksg_window_est(x, y, m, k, 0, nx, ny, c, eps, dxm, dym, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -282,7 +318,7 @@ typedef struct {
     int32_t p;           /* consecutive noise detections before pruning, <= 0: 3      */
     int32_t pruning;     /* 0 off, 1 on                                               */
     int32_t max_steps;   /* LAHC step cap per climb, <= 0: 10000                      */
-    int32_t pad;
+    int32_t chunks;      /* Algorithm 4: number of overlapping chunks n_p, <= 1: none   */
     uint64_t seed;
 } orc_params;
 
@@ -299,6 +335,8 @@ typedef struct {
     int32_t k;
     int32_t score_kind;
     int64_t evals;
+    int32_t estimator;   /* 0: Kraskov 2 (Eq. KSGmi), 1: Kraskov 1 */
+    int32_t pad;
 } orc_series_scorer;
 
 int orc_series_score(void *user, int64_t t_s, int64_t t_e, double *score, double *mi)
@@ -306,8 +344,8 @@ int orc_series_score(void *user, int64_t t_s, int64_t t_e, double *score, double
     orc_series_scorer *s = (orc_series_scorer *)user;
     if (t_s < 0 || t_e >= s->n || t_e < t_s) return ORC_EINVAL;
     orc_mi r;
-    int rc = orc_ksg_window(s->x + t_s, s->y + t_s, t_e - t_s + 1, s->k,
-                            NULL, NULL, NULL, NULL, NULL, NULL, &r);
+    int rc = orc_ksg_window_est(s->x + t_s, s->y + t_s, t_e - t_s + 1, s->k, s->estimator,
+                                NULL, NULL, NULL, NULL, NULL, NULL, &r);
     if (rc != ORC_OK) return rc;
     s->evals++;
     *mi = r.mi;
@@ -564,6 +602,78 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Chunked search (Sec. 7.3, Algorithm 4)                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Algorithm 4 maps the chunks (i - s_max, i + N / n_p), i = 0, N / n_p, 2 N / n_p, ...,
+ * of the series to workers and collects the windows each finds.  Reading: N / n_p is the
+ * integer quotient L (at least 1), a chunk is the half-open range [i - s_max, i + L)
+ * clipped to [t_begin, t_end), the windows are concatenated in chunk order and then
+ * sorted stably by t_s; overlapping windows of neighbouring chunks are all kept.
+ * alg = 0 runs SYCOS_TD on every chunk, 1 SYCOS_BU. */
+typedef struct {
+    orc_window w;
+    int64_t order;
+} orc_ordered;
+
+static int orc_cmp_ordered(const void *a, const void *b)
+{
+    const orc_ordered *u = (const orc_ordered *)a, *v = (const orc_ordered *)b;
+    if (u->w.t_s != v->w.t_s) return (u->w.t_s > v->w.t_s) - (u->w.t_s < v->w.t_s);
+    return (u->order > v->order) - (u->order < v->order);
+}
+
+int orc_search_chunked(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
+                       const orc_params *p, int32_t alg, orc_window *out, int64_t cap,
+                       int64_t *n_out, int64_t *n_evals)
+{
+    int rc = orc_check_params(p, t_begin, t_end);
+    if (rc) return rc;
+    if (alg != 0 && alg != 1) return ORC_EINVAL;
+    int64_t N = t_end - t_begin;
+    int64_t np = p->chunks > 1 ? p->chunks : 1;
+    int64_t L = N / np;
+    if (L < 1) L = 1;
+    orc_params q = *p;
+    q.chunks = 0;
+    orc_window *buf = (orc_window *)malloc(sizeof(orc_window) * 65536);
+    orc_ordered *all = NULL;
+    int64_t n_all = 0, cap_all = 0, evals = 0;
+    if (!buf) return ORC_ENOMEM;
+    for (int64_t i = 0; i < N && rc == ORC_OK; i += L) {
+        int64_t a = t_begin + (i - p->s_max > 0 ? i - p->s_max : 0);
+        int64_t b = t_begin + (i + L < N ? i + L : N);
+        int64_t nw = 0, ne = 0;
+        rc = (alg == 0 ? orc_search_td : orc_search_bu)(f, user, a, b, &q, buf, 65536, &nw, &ne);
+        if (rc) break;
+        evals += ne;
+        for (int64_t j = 0; j < nw; ++j) {
+            if (n_all == cap_all) {
+                int64_t nc = cap_all ? 2 * cap_all : 256;
+                orc_ordered *na = (orc_ordered *)realloc(all, sizeof(orc_ordered) * (size_t)nc);
+                if (!na) { rc = ORC_ENOMEM; break; }
+                all = na;
+                cap_all = nc;
+            }
+            all[n_all].w = buf[j];
+            all[n_all].order = n_all;
+            n_all++;
+        }
+    }
+    free(buf);
+    if (rc == ORC_OK) {
+        if (n_all > 1) qsort(all, (size_t)n_all, sizeof(orc_ordered), orc_cmp_ordered);
+        if (n_out) *n_out = n_all;
+        if (n_evals) *n_evals = evals;
+        if (n_all > cap) rc = ORC_ETRUNC;
+        else
+            for (int64_t j = 0; j < n_all; ++j) out[j] = all[j].w;
+    }
+    free(all);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* iSYCOS selection (Sec. 5.3, Algorithm 3, Eqs. effscore / normalizedeffscore) */
 /* ------------------------------------------------------------------------- */
 
@@ -668,7 +778,11 @@ int orc_search_auto(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
     int32_t sel = s_td > s_bu ? 0 : 1;
     if (selected) *selected = sel;
     int64_t ne = 0;
-    rc = (sel == 0 ? orc_search_td : orc_search_bu)(f, user, t_begin, t_end, p, out, cap, n_out, &ne);
+    /* the selected search over the whole range, in chunks when n_p > 1 (Algorithm 4) */
+    if (p->chunks > 1)
+        rc = orc_search_chunked(f, user, t_begin, t_end, p, sel, out, cap, n_out, &ne);
+    else
+        rc = (sel == 0 ? orc_search_td : orc_search_bu)(f, user, t_begin, t_end, p, out, cap, n_out, &ne);
     if (n_evals) *n_evals = evals + ne;
     return rc;
 }

@@ -79,7 +79,7 @@ class OrcParams(ctypes.Structure):
         ("p", ctypes.c_int32),
         ("pruning", ctypes.c_int32),
         ("max_steps", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("chunks", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
     ]
 
@@ -101,6 +101,8 @@ class OrcSeriesScorer(ctypes.Structure):
         ("k", ctypes.c_int32),
         ("score_kind", ctypes.c_int32),
         ("evals", ctypes.c_int64),
+        ("estimator", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -127,6 +129,10 @@ def lib():
                                     i32p, i32p, i32p, f32p, f32p, f32p]
         L.orc_ksg_window.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int32,
                                      i32p, i32p, i32p, f32p, f32p, f32p, ctypes.POINTER(OrcMI)]
+        L.orc_ksg_window_est.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                         i32p, i32p, i32p, f32p, f32p, f32p, ctypes.POINTER(OrcMI)]
+        L.orc_ksg_point_est.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, i32p, i32p, i32p, f32p, f32p, f32p]
         L.orc_set_mutation.argtypes = [ctypes.c_int32]
         L.orc_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.orc_splitmix64_at.restype = ctypes.c_uint64
@@ -135,6 +141,10 @@ def lib():
             fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                            ctypes.POINTER(OrcParams), ctypes.POINTER(OrcWindow), ctypes.c_int64,
                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.orc_search_chunked.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.POINTER(OrcParams), ctypes.c_int32,
+                                         ctypes.POINTER(OrcWindow), ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.orc_nscores.argtypes = [ctypes.c_double] * 5 + [ctypes.POINTER(ctypes.c_double)] * 2
         L.orc_search_auto.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                       ctypes.POINTER(OrcParams), ctypes.POINTER(OrcSelectParams),
@@ -183,8 +193,9 @@ def fixed_tables(n_max: int):
     return psi, lg
 
 
-def ksg_window(x, y, k: int, points: bool = True):
-    """KSG MI of one window; returns a dict with the scalars and per-point arrays."""
+def ksg_window(x, y, k: int, points: bool = True, estimator: int = 0):
+    """KSG MI of one window (estimator 0: Kraskov's second, Eq. KSGmi; 1: Kraskov's first);
+    returns a dict with the scalars and per-point arrays."""
     x = _f32(x)
     y = _f32(y)
     m = x.shape[0]
@@ -199,8 +210,8 @@ def ksg_window(x, y, k: int, points: bool = True):
                [_ptr(arrs[n], ctypes.c_float) for n in ("eps", "dx", "dy")]
     else:
         ptrs = [None] * 6
-    rc = lib().orc_ksg_window(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), m, k,
-                              *ptrs, ctypes.byref(res))
+    rc = lib().orc_ksg_window_est(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), m, k,
+                                  estimator, *ptrs, ctypes.byref(res))
     if rc != 0:
         raise ValueError("orc_ksg_window failed with %d (m=%d, k=%d)" % (rc, m, k))
     out = {f: getattr(res, f) for f, _ in OrcMI._fields_}
@@ -208,14 +219,14 @@ def ksg_window(x, y, k: int, points: bool = True):
     return out
 
 
-def ksg_point(x, y, k: int, i: int):
+def ksg_point(x, y, k: int, i: int, estimator: int = 0):
     """Counts of one point i of a window (O(m)), for sampled checks of large windows."""
     x = _f32(x)
     y = _f32(y)
     vals = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
             ctypes.c_float(), ctypes.c_float(), ctypes.c_float()]
-    rc = lib().orc_ksg_point(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), x.shape[0], k, i,
-                             *[ctypes.byref(v) for v in vals])
+    rc = lib().orc_ksg_point_est(_ptr(x, ctypes.c_float), _ptr(y, ctypes.c_float), x.shape[0], k,
+                                 estimator, i, *[ctypes.byref(v) for v in vals])
     if rc != 0:
         raise ValueError("orc_ksg_point failed with %d" % rc)
     return dict(zip(("nx", "ny", "c", "eps", "dx", "dy"), [v.value for v in vals]))
@@ -226,11 +237,12 @@ def splitmix64_at(seed: int, n: int) -> int:
 
 
 def make_params(k=4, score_kind=0, sigma=0.2, tau=None, s_min=32, s_max=256, delta_td=0,
-                delta_bu=0, h=8, t_max_idle=3, p=3, pruning=0, max_steps=10000, seed=0):
+                delta_bu=0, h=8, t_max_idle=3, p=3, pruning=0, max_steps=10000, seed=0,
+                chunks=0):
     if tau is None:
         tau = sigma / 4.0
     return OrcParams(k, score_kind, sigma, tau, s_min, s_max, delta_td, delta_bu, h,
-                     t_max_idle, p, pruning, max_steps, 0, seed)
+                     t_max_idle, p, pruning, max_steps, chunks, seed)
 
 
 def _search(fn_name, score, t_begin, t_end, params):
@@ -264,37 +276,75 @@ def _search(fn_name, score, t_begin, t_end, params):
     return wins, n_evals.value
 
 
-def series_scorer(x, y, k: int, score_kind: int = 0):
+def series_scorer(x, y, k: int, score_kind: int = 0, estimator: int = 0):
     x = _f32(x)
     y = _f32(y)
-    user = OrcSeriesScorer(x.ctypes.data, y.ctypes.data, x.shape[0], k, score_kind, 0)
+    user = OrcSeriesScorer(x.ctypes.data, y.ctypes.data, x.shape[0], k, score_kind, 0, estimator, 0)
     user._keep = (x, y)
     return (ctypes.c_void_p(lib().orc_series_score_addr()), user)
 
 
-def search_td(x_or_score, y=None, t_begin=0, t_end=None, **kw):
+def search_td(x_or_score, y=None, t_begin=0, t_end=None, estimator=0, **kw):
     """SYCOS_TD over [t_begin, t_end).  ``x_or_score`` is a series (with ``y``) or a
     callable (t_s, t_e) -> (score, mi) standing in for the window score."""
     params = make_params(**kw)
     if callable(x_or_score):
         score = x_or_score
     else:
-        score = series_scorer(x_or_score, y, params.k, params.score_kind)
+        score = series_scorer(x_or_score, y, params.k, params.score_kind, estimator)
         if t_end is None:
             t_end = len(x_or_score)
     return _search("orc_search_td", score, t_begin, t_end, params)
 
 
-def search_bu(x_or_score, y=None, t_begin=0, t_end=None, **kw):
+def search_bu(x_or_score, y=None, t_begin=0, t_end=None, estimator=0, **kw):
     """SYCOS_BU over [t_begin, t_end); arguments as for :func:`search_td`."""
     params = make_params(**kw)
     if callable(x_or_score):
         score = x_or_score
     else:
-        score = series_scorer(x_or_score, y, params.k, params.score_kind)
+        score = series_scorer(x_or_score, y, params.k, params.score_kind, estimator)
         if t_end is None:
             t_end = len(x_or_score)
     return _search("orc_search_bu", score, t_begin, t_end, params)
+
+
+def search_chunked(x_or_score, y=None, t_begin=0, t_end=None, mode=0, chunks=2, estimator=0, **kw):
+    """Algorithm 4: SYCOS_TD (mode 0) or SYCOS_BU (mode 1) on `chunks` overlapping chunks of
+    [t_begin, t_end); returns (windows, n_evals) like :func:`search_td`."""
+    params = make_params(chunks=chunks, **kw)
+    if callable(x_or_score):
+        score = x_or_score
+    else:
+        score = series_scorer(x_or_score, y, params.k, params.score_kind, estimator)
+        if t_end is None:
+            t_end = len(x_or_score)
+    L = lib()
+    cap = 1 << 16
+    out = (OrcWindow * cap)()
+    n_out = ctypes.c_int64()
+    n_evals = ctypes.c_int64()
+    if isinstance(score, tuple):
+        fptr, user = score
+        rc = L.orc_search_chunked(fptr, ctypes.byref(user), t_begin, t_end, ctypes.byref(params),
+                                  mode, out, cap, ctypes.byref(n_out), ctypes.byref(n_evals))
+    else:
+        def cb(_user, ts, te, sc, mi):
+            try:
+                s_, v_ = score(int(ts), int(te))
+            except Exception:
+                return -1
+            sc[0] = s_
+            mi[0] = v_
+            return 0
+        cfun = SCORE_FN(cb)
+        rc = L.orc_search_chunked(ctypes.cast(cfun, ctypes.c_void_p), None, t_begin, t_end,
+                                  ctypes.byref(params), mode, out, cap, ctypes.byref(n_out),
+                                  ctypes.byref(n_evals))
+    if rc != 0:
+        raise ValueError("orc_search_chunked failed with %d" % rc)
+    wins = [(out[i].t_s, out[i].t_e, out[i].score, out[i].mi) for i in range(n_out.value)]
+    return wins, n_evals.value
 
 
 def nscores(t_td, t_bu, nl_td, ns_bu, alpha=0.5):
@@ -303,11 +353,12 @@ def nscores(t_td, t_bu, nl_td, ns_bu, alpha=0.5):
     return a.value, b.value
 
 
-def search_auto(x, y, t_begin=0, t_end=None, partitions=20, samples=6, alpha=0.5, rho=0.5, **kw):
+def search_auto(x, y, t_begin=0, t_end=None, partitions=20, samples=6, alpha=0.5, rho=0.5,
+                estimator=0, **kw):
     """Algorithm 3 (iSYCOS selection) over [t_begin, t_end); returns (windows, n_evals,
     selected (0 TD / 1 BU), (nscore_TD, nscore_BU))."""
     params = make_params(**kw)
-    score = series_scorer(x, y, params.k, params.score_kind)
+    score = series_scorer(x, y, params.k, params.score_kind, estimator)
     if t_end is None:
         t_end = len(x)
     sp = OrcSelectParams(partitions, samples, alpha, rho)

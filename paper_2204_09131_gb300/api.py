@@ -32,6 +32,7 @@ OPT_INCREMENTAL = 2
 OPT_SERVE_SLOTS = 3
 OPT_SERVE_QUEUE = 4
 OPT_LANES = 5
+OPT_ESTIMATOR = 6
 
 
 class IsycosError(RuntimeError):
@@ -58,7 +59,8 @@ class isycos_params(ctypes.Structure):
                 ("pruning", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sel_partitions", ctypes.c_int32),
                 ("sel_samples", ctypes.c_int32), ("sel_alpha", ctypes.c_double),
-                ("sel_rho", ctypes.c_double)]
+                ("sel_rho", ctypes.c_double), ("chunks", ctypes.c_int32),
+                ("estimator", ctypes.c_int32)]
 
 
 class isycos_query(ctypes.Structure):

@@ -55,6 +55,7 @@ struct BatchArgs {
     int32_t k;
     int32_t nt;                  // threads per CTA of the launch
     int32_t sort_min;            // windows of at least this size take the sorted path
+    int32_t est;                 // 0: Kraskov's second estimator (Eq. KSGmi), 1: the first
 };
 
 // Device-side preparation of a window list held in device memory.
@@ -82,7 +83,7 @@ cudaError_t batched_occupancy(int k, int nt, size_t smem, int *blocks_per_sm);
 cudaError_t set_batched_smem(int k, int nt, size_t smem);
 cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
                          const long long *log_fx, unsigned long long *acc, int32_t *done,
-                         isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                         isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c, int est,
                          cudaStream_t st, int *launches);
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st, int *launches);
 cudaError_t launch_check_finite(const float *d, int64_t n, int32_t *flag, cudaStream_t st);

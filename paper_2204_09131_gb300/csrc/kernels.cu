@@ -65,11 +65,12 @@ __device__ __forceinline__ void list_insert(float (&bd)[K1], int (&bj)[K1], floa
 // Canonical binary64 evaluation of the window scalars from the exact integer sums.
 __device__ __forceinline__ void write_result(isycos_mi_out *o, int k, int m, long long s_psi,
                                              long long s_log, const long long *psi_fx,
-                                             const long long *log_fx) {
+                                             const long long *log_fx, int est) {
     const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
     const double psi_k = __dmul_rn(__ll2double_rn(psi_fx[k]), two_m32);
     const double psi_m = __dmul_rn(__ll2double_rn(psi_fx[m]), two_m32);
-    const double inv_k = __ddiv_rn(1.0, (double)k);
+    // Kraskov's first estimator has no -1/k term (psi_k - 0 is psi_k exactly)
+    const double inv_k = est ? 0.0 : __ddiv_rn(1.0, (double)k);
     const double mean_psi = __ddiv_rn(__dmul_rn(__ll2double_rn(s_psi), two_m32), (double)m);
     const double mi = __dsub_rn(__dadd_rn(__dsub_rn(psi_k, inv_k), psi_m), mean_psi);
     const double ln_m = __dmul_rn(__ll2double_rn(log_fx[m]), two_m32);
@@ -88,7 +89,8 @@ __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, i
                                           int lane, const long long *__restrict__ psi_fx,
                                           const long long *__restrict__ log_fx,
                                           long long &acc_psi, long long &acc_log,
-                                          int32_t *nx_out, int32_t *ny_out, int32_t *c_out) {
+                                          int32_t *nx_out, int32_t *ny_out, int32_t *c_out,
+                                          int est) {
     const float kInf = __int_as_float(0x7f800000);
     float xi[P], yi[P];
     bool val[P];
@@ -156,6 +158,19 @@ __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, i
         }
     }
 
+    // Kraskov's first estimator: both strips of half-width eps_i (the k-th neighbour's
+    // distance, the last of the k + 1 entries with the point itself), points strictly
+    // inside counted: |d| < eps  <=>  |d| <= the float just below eps (eps = 0: none).
+    if (est) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float e = bd[p][K1 - 1];
+            const float t = e > 0.0f ? __int_as_float(__float_as_int(e) - 1) : -1.0f;
+            dxm[p] = t;
+            dym[p] = t;
+        }
+    }
+
     // a4: marginal counts (inclusive; the point itself is counted and removed below).
     int cx[P], cy[P];
 #pragma unroll
@@ -212,8 +227,9 @@ __device__ __forceinline__ void ksg_block(const float2 *__restrict__ s, int m, i
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (!val[p]) continue;
-        const int nxv = cx[p] - 1, nyv = cy[p] - 1;
-        acc_psi += __ldg(psi_fx + nxv) + __ldg(psi_fx + nyv);
+        // the point itself was counted unless the strips are empty (estimator 1, eps = 0)
+        const int nxv = max(cx[p] - 1, 0), nyv = max(cy[p] - 1, 0);
+        acc_psi += __ldg(psi_fx + nxv + est) + __ldg(psi_fx + nyv + est);
         acc_log += __ldg(log_fx + cc[p]);
         const int i = base + p * 32 + lane;
         if (nx_out) {
@@ -287,7 +303,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                                   const long long *__restrict__ psi_fx,
                                   const long long *__restrict__ log_fx, long long &acc_psi,
                                   long long &acc_log, int32_t *nx_out, int32_t *ny_out,
-                                  int32_t *c_out) {
+                                  int32_t *c_out, int est) {
     const float kInf = __int_as_float(0x7f800000);
     const int N = pow2_ceil(m);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
@@ -381,6 +397,10 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                     dym = fmaxf(dym, fabsf(yi - v.y));
                     cc += bd[r] == 0.0f ? 1 : 0;
                 }
+                if (est) {   // Kraskov's first estimator: strict strips of half-width eps
+                    const float e = bd[K1 - 1];
+                    dxm = dym = e > 0.0f ? __int_as_float(__float_as_int(e) - 1) : -1.0f;
+                }
                 pdx[t] = dxm;
                 pdy[t] = dym;
                 pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
@@ -436,8 +456,9 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
             for (int u = t - 1; u >= 0 && rec[u].x == xi; --u) cc += rec[u].y == yi ? 1 : 0;
             for (int u = t + 1; u < m && rec[u].x == xi; ++u) cc += rec[u].y == yi ? 1 : 0;
         }
+        // (an empty strip, t < 0, leaves the search ranges at the point itself: count 1)
         const int nxv = cx - 1, nyv = cy - 1;
-        acc_psi += __ldg(psi_fx + nxv) + __ldg(psi_fx + nyv);
+        acc_psi += __ldg(psi_fx + nxv + est) + __ldg(psi_fx + nyv + est);
         acc_log += __ldg(log_fx + cc);
         if (nx_out) {
             nx_out[ji] = nxv;
@@ -491,11 +512,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
             }
             if (per_job == 1 && it.m >= a.sort_min && it.m <= kSortMax) {
                 ksg_window_sorted<K1, NT>(s, it.m, reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m),
-                                          a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+                                          a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
             } else {
                 const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
                 for (int b = sub; b < nblk; b += wpw)
-                    ksg_block<K1>(s, it.m, b * kBlockPts, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+                    ksg_block<K1>(s, it.m, b * kBlockPts, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
             }
             lp = warp_sum64(lp);
             ll = warp_sum64(ll);
@@ -506,7 +527,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         }
         __syncthreads();
         if (has && sub == 0 && lane == 0)
-            write_result(a.out + it.out, a.k, it.m, acc_psi[slot], acc_log[slot], a.psi_fx, a.log_fx);
+            write_result(a.out + it.out, a.k, it.m, acc_psi[slot], acc_log[slot], a.psi_fx, a.log_fx, a.est);
     }
     // Small windows (m <= 64): one warp each, staged in the warp's own slice, no CTA barrier.
     float2 *ws = tile + warp * kBlockPts;
@@ -528,12 +549,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
             co = a.c + it.pts;
         }
         if (it.m <= 32)
-            ksg_block<K1, 1>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            ksg_block<K1, 1>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
         else
-            ksg_block<K1, 2>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co);
+            ksg_block<K1, 2>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
         lp = warp_sum64(lp);
         ll = warp_sum64(ll);
-        if (lane == 0) write_result(a.out + it.out, a.k, it.m, lp, ll, a.psi_fx, a.log_fx);
+        if (lane == 0) write_result(a.out + it.out, a.k, it.m, lp, ll, a.psi_fx, a.log_fx, a.est);
     }
     // The last CTA to finish zeroes the work counters for the next launch on this buffer:
     // every other CTA has taken its last job before it counts itself out.
@@ -556,7 +577,7 @@ __global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const
                                                        const long long *log_fx,
                                                        unsigned long long *acc, int32_t *done,
                                                        isycos_mi_out *out, int32_t *nx,
-                                                       int32_t *ny, int32_t *c) {
+                                                       int32_t *ny, int32_t *c, int est) {
     extern __shared__ float2 tile[];
     constexpr int W = NT / 32;
     __shared__ long long sp[W], sl[W];
@@ -567,7 +588,7 @@ __global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const
     long long lp = 0, ll = 0;
     const int b = blockIdx.x * W + warp;
     const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
-    if (b < nblk) ksg_block<K1>(tile, it.m, b * kBlockPts, lane, psi_fx, log_fx, lp, ll, nx, ny, c);
+    if (b < nblk) ksg_block<K1>(tile, it.m, b * kBlockPts, lane, psi_fx, log_fx, lp, ll, nx, ny, c, est);
     lp = warp_sum64(lp);
     ll = warp_sum64(ll);
     if (lane == 0) {
@@ -591,7 +612,7 @@ __global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const
         __threadfence();
         const long long tp = (long long)atomicAdd(acc, 0ull);
         const long long tl = (long long)atomicAdd(acc + 1, 0ull);
-        write_result(out, k, it.m, tp, tl, psi_fx, log_fx);
+        write_result(out, k, it.m, tp, tl, psi_fx, log_fx, est);
         acc[0] = 0;
         acc[1] = 0;
         *done = 0;
@@ -684,7 +705,7 @@ struct BatchedTable {
 };
 
 using PlainFn = void (*)(WorkItem, int, const long long *, const long long *, unsigned long long *,
-                         int32_t *, isycos_mi_out *, int32_t *, int32_t *, int32_t *);
+                         int32_t *, isycos_mi_out *, int32_t *, int32_t *, int32_t *, int);
 constexpr int kPlainNT = 256;
 
 PlainFn plain_fn(int k) {
@@ -734,7 +755,7 @@ cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream
 cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
                          const long long *log_fx, unsigned long long *acc, int32_t *done,
                          isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
-                         cudaStream_t st, int *launches) {
+                         int est, cudaStream_t st, int *launches) {
     PlainFn fn = plain_fn(k);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = (size_t)it.m * 8;
@@ -744,7 +765,7 @@ cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
     }
     const int per_cta = (kPlainNT / 32) * kBlockPts;
     const int grid = (it.m + per_cta - 1) / per_cta;
-    fn<<<grid, kPlainNT, smem, st>>>(it, k, psi_fx, log_fx, acc, done, out, nx, ny, c);
+    fn<<<grid, kPlainNT, smem, st>>>(it, k, psi_fx, log_fx, acc, done, out, nx, ny, c, est);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

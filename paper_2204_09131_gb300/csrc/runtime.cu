@@ -160,9 +160,9 @@ static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, in
     return ISYCOS_OK;
 }
 
-isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
-                          isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
-                          cudaStream_t st) {
+isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
+                            int est, int32_t *nx, int32_t *ny, int32_t *c, cudaStream_t st) {
+    L.open.open = false;
     if (n <= 0) return ISYCOS_OK;
     if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
     int max_m = 0, max_sorted = 0;
@@ -231,7 +231,6 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     a.psi_fx = ctx->d_psi_fx;
     a.log_fx = ctx->d_log_fx;
     // results go straight to the pinned, mapped host buffer (no copy back)
-    isycos_mi_out *h_out = reinterpret_cast<isycos_mi_out *>(L.h_table.p);
     a.out = reinterpret_cast<isycos_mi_out *>(L.h_table.dev);
     a.nx = nx ? reinterpret_cast<int32_t *>(L.d_nx.p) : nullptr;
     a.ny = nx ? reinterpret_cast<int32_t *>(L.d_ny.p) : nullptr;
@@ -239,6 +238,7 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
     a.k = k;
     a.nt = nt;
     a.sort_min = sort_min;
+    a.est = est;
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
@@ -250,8 +250,30 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
         e = cudaMemcpyAsync(nx, L.d_nx.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ny, L.d_ny.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c, L.d_c.p, 4 * total_pts, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) {
+            L.queue_clean = false;
+            return cuda_fail(ctx, e, "per-point results");
+        }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    Lane::Open &o = L.open;
+    o.open = true;
+    o.st = st;
+    o.n = n;
+    o.pairs = pairs;
+    o.total_pts = total_pts;
+    o.nx = nx;
+    o.ny = ny;
+    o.c = c;
+    o.max_m = max_m;
+    for (int q = 0; q < kBuckets; ++q) o.count[q] = count[q];
+    return ISYCOS_OK;
+}
+
+isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out) {
+    Lane::Open &o = L.open;
+    if (!o.open) return ISYCOS_OK;
+    o.open = false;
+    cudaError_t e = cudaStreamSynchronize(o.st);
     float t0 = 0.0f, t1 = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ctx->ev_ref, L.ev_start);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev_ref, L.ev_stop);
@@ -259,20 +281,28 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
         L.queue_clean = false;
         return cuda_fail(ctx, e, "MI kernel");
     }
-    memcpy(out, h_out, sizeof(isycos_mi_out) * n);
-    add_stats(ctx, n, pairs, 1, 1, 0);
+    memcpy(out, L.h_table.p, sizeof(isycos_mi_out) * o.n);
+    add_stats(ctx, o.n, o.pairs, 1, 1, 0);
     {
         // kernel intervals on the device timeline (lanes may overlap); their union is the
         // kernel's busy time reported by isycos_get_stats
         std::lock_guard<std::mutex> g(ctx->stats_mu);
         ctx->kernel_iv.push_back({t0, t1});
         ctx->stats.mi_kernel_launches += 1;
-        for (int q = 0; q < kBuckets; ++q) ctx->stats.windows_by_size[kBuckets - 1 - q] += count[q];
-        const int bmax = kBuckets - 1 - bucket_slot(max_m);
+        for (int q = 0; q < kBuckets; ++q) ctx->stats.windows_by_size[kBuckets - 1 - q] += o.count[q];
+        const int bmax = kBuckets - 1 - bucket_slot(o.max_m);
         ctx->stats.launches_by_size[bmax] += 1;
         ctx->stats.launch_ms_by_size[bmax] += (double)(t1 - t0);
     }
     return ISYCOS_OK;
+}
+
+isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
+                          isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
+                          cudaStream_t st, int est) {
+    isycos_status rc = engine_launch(ctx, L, w, n, k, est, nx, ny, c, st);
+    if (rc) return rc;
+    return engine_collect(ctx, L, out);
 }
 
 isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out) {
@@ -382,6 +412,8 @@ void isycos_params_default(isycos_params *p) {
     p->sel_samples = 6;
     p->sel_alpha = 0.5;
     p->sel_rho = 0.5;
+    p->chunks = 1;
+    p->estimator = 0;
 }
 
 isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budget_bytes) {
@@ -581,7 +613,7 @@ isycos_status isycos_mi_windows(isycos_ctx *ctx, const isycos_window *windows, i
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
     return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
-                       pick_stream(ctx, cuda_stream));
+                       pick_stream(ctx, cuda_stream), ctx->opt_estimator);
 }
 
 isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *windows,
@@ -596,7 +628,7 @@ isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *win
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
     return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nx, ny, c,
-                       pick_stream(ctx, cuda_stream));
+                       pick_stream(ctx, cuda_stream), ctx->opt_estimator);
 }
 
 isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_windows,
@@ -660,6 +692,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.k = k;
     a.nt = nt;
     a.sort_min = sort_min;
+    a.est = ctx->opt_estimator;
     e = launch_batched(a, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
     add_stats(ctx, n_w, 0, launches + 1, 1, 0);
@@ -715,7 +748,7 @@ isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *wind
         it.pts = -1;
         pairs += (int64_t)it.m * (it.m - 1);
         cudaError_t e = launch_plain(it, k, ctx->d_psi_fx, ctx->d_log_fx, acc, done, d_out + i,
-                                     nullptr, nullptr, nullptr, st, &launches);
+                                     nullptr, nullptr, nullptr, ctx->opt_estimator, st, &launches);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "plain MI kernel launch");
     }
     cudaError_t e = cudaMemcpyAsync(out, d_out, sizeof(isycos_mi_out) * n_w, cudaMemcpyDeviceToHost, st);
@@ -786,8 +819,12 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) 
             ctx->serve_queue = (int)value;
             return ISYCOS_OK;
         case ISYCOS_OPT_LANES:
-            if (value < 1 || value > 64) break;
+            if (value < 1 || value > kMaxLanes) break;
             ctx->max_lanes = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_ESTIMATOR:
+            if (value < 0 || value > 1) break;
+            ctx->opt_estimator = (int)value;
             return ISYCOS_OK;
         default:
             return fail(ctx, ISYCOS_E_INVAL, "unknown option %d", option);

@@ -41,6 +41,15 @@ struct Lane {
     DevBuf d_chain_desc, d_chain_steps, d_chain_state, d_chain_recomp, d_chain_out;
     HostBuf h_items, h_table;          // pinned staging: table + items; results
     bool queue_clean = false;          // d_queue holds zeroed work counters
+    // the open launch of engine_launch
+    struct Open {
+        bool open = false;
+        cudaStream_t st = nullptr;
+        int64_t n = 0, pairs = 0, total_pts = 0;
+        int32_t *nx = nullptr, *ny = nullptr, *c = nullptr;
+        int32_t count[15] = {0};
+        int max_m = 0;
+    } open;
     std::vector<int32_t> h_slot;       // per-call bucket slots (reused)
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
 };
@@ -92,6 +101,7 @@ struct isycos_ctx {
     // Options.
     int opt_kernel = 0;
     int opt_incremental = 1;
+    int opt_estimator = 0;   // estimator of the direct window-MI entry points
     int serve_slots = 64;
     int serve_queue = 100000;
 
@@ -116,7 +126,16 @@ isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k);
 // in input order into the host array `out`.  Per-point arrays (host) are optional.
 isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                           isycos_mi_out *out, int32_t *nx, int32_t *ny, int32_t *c,
-                          cudaStream_t st);
+                          cudaStream_t st, int est = 0);
+// The same in two halves: engine_launch stages and launches (asynchronous on st), and
+// engine_collect waits for that launch and writes the results.  One launch per lane may be
+// open at a time.
+isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
+                            int est, int32_t *nx, int32_t *ny, int32_t *c, cudaStream_t st);
+isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out);
+
+// Lane indices: searches use 0 .. kMaxLanes - 1, serving workers kServeLaneBase + worker.
+constexpr int kMaxLanes = 16;
 
 // Lane i of the context (created on first use; lane 0 runs on ctx->stream).
 isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out);

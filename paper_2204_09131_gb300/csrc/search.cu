@@ -54,6 +54,11 @@ isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchPar
     o->sel_alpha = in->sel_alpha >= 0.0 ? in->sel_alpha : 0.5;
     o->sel_rho = in->sel_rho > 0.0 ? in->sel_rho : 0.5;
     if (o->sel_partitions > (1 << 20)) return fail(ctx, ISYCOS_E_INVAL, "sel_partitions too large");
+    o->chunks = in->chunks > 1 ? in->chunks : 1;
+    if (o->chunks > (1 << 20)) return fail(ctx, ISYCOS_E_INVAL, "chunks too large");
+    o->estimator = in->estimator;
+    if (o->estimator != 0 && o->estimator != 1)
+        return fail(ctx, ISYCOS_E_INVAL, "estimator must be 0 or 1");
     return ISYCOS_OK;
 }
 
@@ -229,6 +234,7 @@ public:
         asked_.clear();
         dest_.clear();
         next_chain_ = 0;
+        ++round_;
         for (;;) {
             if (finished_) return false;
             if (phase_ == kStart) {
@@ -239,16 +245,23 @@ public:
                 ws_ = c_;
                 we_ = c_ + prm.s_min - 1;
                 invalidate_rings();
-                grid_.reset(ws_, we_, prm.delta_bu);
-                grid_.follow(ws_, we_, prm.t_max_idle + 2);
+                // scores are pure functions of the window: keep the cells of earlier climbs
+                // when this start lies on their lattice
+                if (!grid_.on_lattice(ws_, we_, prm.delta_bu)) {
+                    grid_.reset(ws_, we_, prm.delta_bu);
+                    spec_starts_.clear();
+                }
+                if (spec_starts_.size() > 256) spec_starts_.clear();   // starts behind the cursor
                 // a climb always evaluates ring N_1 of its first window next: ask it now
-                if (!lookup(ws_, (int32_t)(we_ - ws_ + 1), &start_val_))
-                    ask(ws_, we_, kDestStart, -1, false);
+                int64_t ac, bc;
+                grid_.centre(ws_, we_, &ac, &bc);
+                if (!grid_.get(ac, bc, &start_val_)) ask_cell(ac, bc, ws_, we_, kDestStart, -1, -1);
                 if (prm.t_max_idle >= 0 && prm.max_steps > 0)
                     for (int rr = 1; rr <= std::min(prm.t_max_idle + 1, spec_depth()); ++rr)
                         ask_ring(rr, false, false);
                 phase_ = kWaitStart;
                 if (asked_.empty()) continue;
+                speculate_next_climbs();
                 break;
             }
             if (phase_ == kWaitStart) {
@@ -265,11 +278,12 @@ public:
                 // climb moves by one delta and the remaining rings when it does not.
                 r_last = std::max(r_last, std::min(prm.t_max_idle + 1, spec_depth()));
                 const size_t before = asked_.size();
-                grid_.follow(ws_, we_, prm.t_max_idle + 2);   // every ring of this centre
                 ask_ring(r, dropped_[0], dropped_[1]);
                 // speculate only when this step needs a round trip anyway
-                if (asked_.size() > before)
+                if (asked_.size() > before) {
                     for (int rr = r + 1; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1]);
+                    speculate_next_climbs();
+                }
                 phase_ = kDecide;
                 if (asked_.empty()) continue;
                 break;
@@ -292,16 +306,15 @@ public:
         for (size_t i = 0; i < n && i < dest_.size(); ++i) {
             const Dest &d = dest_[i];
             const Val v{score_of(res[i]), res[i].mi};
-            if (d.kind == kDestStart) {
-                start_val_ = v;
-                cache_.put(key(d.ts, (int32_t)(d.te - d.ts + 1)), v);
-            } else if (d.kind == kDestCell) {
-                grid_.val[(size_t)d.idx] = v;   // the cell index taken when it was asked
-                grid_.tag[(size_t)d.idx] = grid_.gen;
+            if (d.kind == kDestStart || d.kind == kDestCell) {
+                if (d.kind == kDestStart) start_val_ = v;
+                grid_.put(d.a, d.b, v);
             } else if (d.kind == kDestExt) {
-                rings_[d.r].ext_val[d.idx] = v;
-                rings_[d.r].ext_have[d.idx] = 1;
-                cache_.put(key(d.ts, (int32_t)(d.te - d.ts + 1)), v);
+                if (d.r >= 0) {
+                    rings_[d.r].ext_val[d.side] = v;
+                    rings_[d.r].ext_have[d.side] = 1;
+                }
+                ext_.put(d.a, d.b, v);
             }
         }
     }
@@ -311,86 +324,124 @@ public:
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
         rings_.resize((size_t)prm.t_max_idle + 2);
-        grid_.init(2 * (prm.t_max_idle + 2) + 2);
+        // a round reaches at most T_maxIdle + 1 cells around the window, and the speculative
+        // climbs some s_min / delta cells beyond it
+        grid_.init(4 * (prm.t_max_idle + 2) + 8 * std::max<int64_t>(1, prm.s_min / std::max(1, prm.delta_bu)));
     }
 
 private:
     enum Phase { kStart, kWaitStart, kRing, kDecide };
     enum DestKind { kDestStart, kDestCell, kDestExt, kDestNone };
     struct Dest {
-        int kind, r, idx;
-        int64_t ts, te;
+        int kind, r, side;
+        int64_t a, b;   // grid cell, or (start, size) of an extension window
     };
-    // Scores of this climb's windows on its delta grid: window [c + a d, c + s_min - 1 + b d]
-    // at cell (a, b) of a square array that follows the current window.
+    // Scores of windows on the delta lattice of the climbs: window [bs + a d, be + b d] at
+    // cell (a, b).  The array is direct mapped (cell (a, b) in slot (a mod G, b mod G), with
+    // its coordinates kept to tell it from the cells that share the slot), so it follows the
+    // search along the series without copying.
     struct GridCache {
-        int G = 64;
+        int G = 64, lg = 6;
         int64_t bs = 0, be = 0, d = 1;
-        int64_t a0 = 0, b0 = 0;   // offsets of cell (0, 0)
         uint32_t gen = 1;
+        bool valid = false;
         std::vector<Val> val;
-        std::vector<uint32_t> tag;
+        std::vector<uint32_t> tag;     // == gen: val holds the score of cell (ka, kb)
+        std::vector<uint32_t> asked;   // round in which (ka, kb) was last asked
+        std::vector<int64_t> ka, kb;
         void init(int min_side) {
-            G = std::max(64, min_side);
+            G = 64;
+            lg = 6;
+            while (G < min_side) {
+                G <<= 1;
+                ++lg;
+            }
             val.assign((size_t)G * G, Val{0.0, 0.0});
             tag.assign((size_t)G * G, 0);
+            asked.assign((size_t)G * G, 0);
+            ka.assign((size_t)G * G, 0);
+            kb.assign((size_t)G * G, 0);
+        }
+        bool on_lattice(int64_t ws, int64_t we, int64_t delta) const {
+            return valid && delta == d && (ws - bs) % d == 0 && (we - be) % d == 0;
         }
         void reset(int64_t s, int64_t e, int64_t delta) {
             bs = s;
             be = e;
             d = delta;
-            a0 = b0 = -G / 2;
             ++gen;
+            valid = true;
         }
-        bool cell(int64_t ts, int64_t te, size_t *idx) const {
-            const int64_t da = ts - bs, db = te - be;
-            if (da % d != 0 || db % d != 0) return false;
-            const int64_t a = da / d - a0, b = db / d - b0;
-            if (a < 0 || a >= G || b < 0 || b >= G) return false;
-            *idx = (size_t)a * G + (size_t)b;
-            return true;
+        void centre(int64_t ws, int64_t we, int64_t *a, int64_t *b) const {
+            *a = (ws - bs) / d;
+            *b = (we - be) / d;
         }
-        bool get(int64_t ts, int64_t te, Val *v) const {
-            size_t i;
-            if (!cell(ts, te, &i) || tag[i] != gen) return false;
+        size_t slot(int64_t a, int64_t b) const {
+            return ((size_t)(a & (G - 1)) << lg) | (size_t)(b & (G - 1));
+        }
+        bool get(int64_t a, int64_t b, Val *v) const {
+            const size_t i = slot(a, b);
+            if (tag[i] != gen || ka[i] != a || kb[i] != b) return false;
             *v = val[i];
             return true;
         }
-        void put(int64_t ts, int64_t te, const Val &v) {
-            size_t i;
-            if (!cell(ts, te, &i)) return;
+        bool known(int64_t a, int64_t b) const {
+            const size_t i = slot(a, b);
+            return tag[i] == gen && ka[i] == a && kb[i] == b;
+        }
+        // mark (a, b) as asked in round `round`; false if it already was
+        bool mark(int64_t a, int64_t b, uint32_t round) {
+            const size_t i = slot(a, b);
+            if (asked[i] == round && ka[i] == a && kb[i] == b) return false;
+            if (ka[i] != a || kb[i] != b) tag[i] = 0;   // the slot now belongs to (a, b)
+            asked[i] = round;
+            ka[i] = a;
+            kb[i] = b;
+            return true;
+        }
+        void put(int64_t a, int64_t b, const Val &v) {
+            const size_t i = slot(a, b);
             val[i] = v;
             tag[i] = gen;
+            ka[i] = a;
+            kb[i] = b;
         }
-        // Cell of offset (a, b) from the window (ws, we), which lies on the grid and whose
-        // square of half-side max(|a|, |b|) + 1 is inside the array (after follow()).
-        size_t near(int64_t ac, int64_t bc, int a, int b) const {
-            return (size_t)(ac + a - a0) * G + (size_t)(bc + b - b0);
+    };
+    // Scores of noise-test extension windows (start, size): a small direct-mapped cache.
+    struct ExtCache {
+        static constexpr int N = 4096;
+        struct E {
+            int64_t s = -1, m = 0;
+            uint32_t asked = 0;
+            bool have = false;
+            Val v{0.0, 0.0};
+        };
+        std::vector<E> e = std::vector<E>(N);
+        static size_t slot(int64_t s, int64_t m) {
+            uint64_t k = ((uint64_t)s * 0x9E3779B97F4A7C15ULL) ^ ((uint64_t)m * 0xC2B2AE3D27D4EB4FULL);
+            return (size_t)(k >> 52) & (N - 1);
         }
-        void centre(int64_t ws, int64_t we, int64_t *ac, int64_t *bc) const {
-            *ac = (ws - bs) / d;
-            *bc = (we - be) / d;
+        bool get(int64_t s, int64_t m, Val *v) const {
+            const E &x = e[slot(s, m)];
+            if (!x.have || x.s != s || x.m != m) return false;
+            *v = x.v;
+            return true;
         }
-        // keep the square of half-side R around the window (ws, we) inside the array
-        void follow(int64_t ws, int64_t we, int R) {
-            const int64_t ac = (ws - bs) / d, bc = (we - be) / d;
-            if (ac - R >= a0 && ac + R < a0 + G && bc - R >= b0 && bc + R < b0 + G) return;
-            std::vector<Val> nv((size_t)G * G);
-            std::vector<uint32_t> nt((size_t)G * G, 0);
-            const int64_t na0 = ac - G / 2, nb0 = bc - G / 2;
-            for (int64_t a = 0; a < G; ++a)
-                for (int64_t b = 0; b < G; ++b) {
-                    const size_t i = (size_t)a * G + (size_t)b;
-                    if (tag[i] != gen) continue;
-                    const int64_t ga = a + a0 - na0, gb = b + b0 - nb0;
-                    if (ga < 0 || ga >= G || gb < 0 || gb >= G) continue;
-                    nv[(size_t)ga * G + (size_t)gb] = val[i];
-                    nt[(size_t)ga * G + (size_t)gb] = gen;
-                }
-            val.swap(nv);
-            tag.swap(nt);
-            a0 = na0;
-            b0 = nb0;
+        bool mark(int64_t s, int64_t m, uint32_t round) {
+            E &x = e[slot(s, m)];
+            if (x.s == s && x.m == m && (x.have || x.asked == round)) return false;
+            if (x.s != s || x.m != m) x.have = false;
+            x.s = s;
+            x.m = m;
+            x.asked = round;
+            return true;
+        }
+        void put(int64_t s, int64_t m, const Val &v) {
+            E &x = e[slot(s, m)];
+            x.s = s;
+            x.m = m;
+            x.have = true;
+            x.v = v;
         }
     };
     // Ring N_r asked around the centre (cs, ce).  Its windows' scores are cells of the grid
@@ -402,9 +453,14 @@ private:
         char ext_have[2] = {0, 0};
     };
 
-    void ask(int64_t ts, int64_t te, int kind, int r, bool base, int idx = 0, int32_t chain = -1) {
-        asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), chain, base});
-        dest_.push_back(Dest{base ? (int)kDestNone : kind, r, idx, ts, te});
+    void ask_cell(int64_t a, int64_t b, int64_t ts, int64_t te, int kind, int r, int32_t chain) {
+        asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), chain, false});
+        dest_.push_back(Dest{kind, r, 0, a, b});
+        grid_.mark(a, b, round_);
+    }
+    void ask_ext(int64_t ts, int64_t te, int r, int side) {
+        asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), -1, false});
+        dest_.push_back(Dest{kDestExt, r, side, ts, te - ts + 1});
     }
 
     void invalidate_rings() {
@@ -447,9 +503,11 @@ private:
         auto visit = [&](int a, int b) {
             int64_t ts, te;
             if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
-            const size_t ci = grid_.near(ac, bc, a, b);
-            if (grid_.tag[ci] == grid_.gen) return;   // evaluated earlier in this climb
-            ask(ts, te, kDestCell, r, false, (int)ci, chain);
+            if (grid_.known(ac + a, bc + b)) return;                 // evaluated earlier
+            const size_t i = grid_.slot(ac + a, bc + b);
+            if (grid_.asked[i] == round_ && grid_.ka[i] == ac + a && grid_.kb[i] == bc + b)
+                return;                                               // asked in this round
+            ask_cell(ac + a, bc + b, ts, te, kDestCell, r, chain);
         };
         for (int b = -r; b <= r; ++b) visit(-r, b);
         for (int a = -r + 1; a <= r; ++a) visit(a, r);
@@ -457,7 +515,7 @@ private:
         for (int a = r - 1; a > -r; --a) visit(a, -r);
         if (asked_.size() > first + 1) {
             asked_.insert(asked_.begin() + first, WinReq{ws_, (int32_t)(we_ - ws_ + 1), chain, true});
-            dest_.insert(dest_.begin() + first, Dest{kDestNone, r, 0, ws_, we_});
+            dest_.insert(dest_.begin() + first, Dest{kDestNone, r, 0, 0, 0});
         } else if (asked_.size() == first + 1) {
             asked_.back().chain = -1;
         }
@@ -468,19 +526,74 @@ private:
             for (int sd = 0; sd < 2; ++sd) {
                 if (!keep(sd == 0 ? -r : 0, sd == 0 ? 0 : r, r, drop_left, drop_right, &ts, &te)) continue;
                 Val v;
-                if (lookup(es[sd], (int32_t)(ee[sd] - es[sd] + 1), &v)) {
+                if (ext_.get(es[sd], ee[sd] - es[sd] + 1, &v)) {
                     g.ext_val[sd] = v;
                     g.ext_have[sd] = 1;
                 } else {
-                    ask(es[sd], ee[sd], kDestExt, r, false, sd);
+                    ext_.mark(es[sd], ee[sd] - es[sd] + 1, round_);
+                    ask_ext(es[sd], ee[sd], r, sd);
                 }
             }
         }
     }
 
+    // Speculation across climbs.  Most climbs end where they stand; the next climb then starts
+    // at max(t_e + 1, c + s_min) with a window of s_min points and first asks its start
+    // window and rings.  When a round goes to the GPU anyway, also ask those windows for the
+    // next kSpecClimbs climbs, assuming each ends at its start.  Their scores are cached and
+    // read only if a climb does start there; the decisions are unchanged.
+    static constexpr int kSpecClimbs = 3;
+    void speculate_next_climbs() {
+        if (prm.t_max_idle < 0 || prm.max_steps <= 0) return;
+        const int64_t d = prm.delta_bu, sm = prm.s_min;
+        const int depth = std::min(prm.t_max_idle + 1, spec_depth_for(sm));
+        int64_t c = std::max(we_ + 1, c_ + sm);
+        for (int j = 0; j < kSpecClimbs; ++j, c += sm) {
+            if (c + sm > t_end) return;
+            const int64_t cs = c, ce = c + sm - 1;
+            if (!grid_.on_lattice(cs, ce, d)) return;   // cached only on the grid's lattice
+            Val seen;
+            if (spec_starts_.find((uint64_t)c, &seen)) continue;   // asked in an earlier round
+            spec_starts_.put((uint64_t)c, Val{0.0, 0.0});
+            int64_t ac, bc;
+            grid_.centre(cs, ce, &ac, &bc);
+            spec_cell(ac, bc, cs, ce);
+            for (int r = 1; r <= depth; ++r) {
+                for (int a = -r; a <= r; ++a)
+                    for (int b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
+                        const int64_t ts = cs + a * d, te = ce + b * d, mm = te - ts + 1;
+                        if (mm < prm.s_min || mm > prm.s_max) continue;
+                        if (ts < t_begin || te > t_end - 1 || ts <= last_end_) continue;
+                        spec_cell(ac + a, bc + b, ts, te);
+                    }
+                if (prm.pruning && (int64_t)r * d >= prm.k + 1) {
+                    const int64_t span = (int64_t)r * d;
+                    if (cs - span >= t_begin && cs - span > last_end_) spec_ext(cs - span, cs - 1);
+                    if (ce + span <= t_end - 1) spec_ext(ce + 1, ce + span);
+                }
+            }
+        }
+    }
+    void spec_cell(int64_t a, int64_t b, int64_t ts, int64_t te) {
+        if (grid_.known(a, b)) return;
+        const size_t i = grid_.slot(a, b);
+        if (grid_.asked[i] == round_ && grid_.ka[i] == a && grid_.kb[i] == b) return;
+        // never take a slot that holds a cell asked in this round
+        if (grid_.asked[i] == round_) return;
+        ask_cell(a, b, ts, te, kDestCell, -1, -1);
+    }
+    void spec_ext(int64_t ts, int64_t te) {
+        const int64_t m = te - ts + 1;
+        if (m < prm.k + 1) return;
+        Val v;
+        if (ext_.get(ts, m, &v)) return;
+        if (!ext_.mark(ts, m, round_)) return;
+        ask_ext(ts, te, -1, 0);
+    }
+
     // Rings asked per round for the current window size (speculation depth).
-    int spec_depth() const {
-        const int64_t m = we_ - ws_ + 1;
+    int spec_depth() const { return spec_depth_for(we_ - ws_ + 1); }
+    static int spec_depth_for(int64_t m) {
         if (m <= 256) return 4;
         if (m <= 2048) return 2;
         return 1;
@@ -516,15 +629,14 @@ private:
             for (int64_t b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
                 int64_t ts, te;
                 if (!keep(a, b, r, dropped_[0], dropped_[1], &ts, &te)) continue;
-                const size_t ci = grid_.near(ac, bc, (int)a, (int)b);
-                if (grid_.tag[ci] != grid_.gen) {
-                    // only when the cache moved away from this centre since the ring was
-                    // asked: ask it again
+                Val v;
+                if (!grid_.get(ac + a, bc + b, &v)) {
+                    // only when another cell took the slot since the ring was asked: ask it
+                    // again
                     phase_ = kRing;
                     rings_[r].asked = false;
                     return;
                 }
-                const Val &v = grid_.val[ci];
                 count(te - ts + 1);
                 if (!have || v.score > bv.score) {        // first maximum wins
                     have = true;
@@ -581,7 +693,6 @@ private:
         c_ = std::max(we_ + 1, c_ + prm.s_min);
         ++climb_;
         phase_ = kStart;
-        if (cache_.size() > 4096) cache_.clear();   // O(1): generation bump
     }
 
     void finish() {
@@ -603,6 +714,9 @@ private:
     std::vector<Ring> rings_;
     std::vector<Dest> dest_;
     GridCache grid_;
+    ExtCache ext_;
+    uint32_t round_ = 0;
+    FlatCache spec_starts_;   // climb starts whose windows were asked speculatively
     int32_t next_chain_ = 0;
 };
 
@@ -684,6 +798,7 @@ public:
             for (int i = 0; i < ms; ++i) {
                 const int64_t a = t_begin + (int64_t)idx[i] * L;
                 SearchParams p = prm;
+                p.chunks = 1;   // the samples are searched whole
                 for (int mode = 0; mode < 2; ++mode) {
                     p.mode = mode;
                     subs_.push_back(make_machine(xs, ys, a, a + L, p));
@@ -738,10 +853,94 @@ private:
     std::unique_ptr<SearchMachine> final_;
 };
 
+// ---------------------------------------------------------------------------------------
+// Chunked search (Sec. 7.3, Algorithm 4)
+// ---------------------------------------------------------------------------------------
+// The range is cut into overlapping chunks [i - s_max, i + L) for i = 0, L, 2L, ... (L =
+// floor(length / n_p), clipped to the range); the selected search runs on every chunk
+// independently (their frontiers batched together), and the windows of all chunks are
+// concatenated in chunk order and sorted by t_s (stable).  Windows found by neighbouring
+// chunks may overlap, as in the paper's collected result.
+class ChunkMachine : public SearchMachine {
+public:
+    bool want(std::vector<WinReq> &req) override {
+        bool any = false;
+        int32_t chain_base = 0;
+        from_.clear();
+        for (size_t i = 0; i < subs_.size(); ++i) {
+            if (done_[i]) continue;
+            std::vector<WinReq> r;
+            if (!subs_[i]->want(r)) {
+                done_[i] = true;
+                continue;
+            }
+            int32_t top = 0;
+            for (WinReq &w : r)
+                if (w.chain >= 0) {
+                    top = std::max(top, w.chain + 1);
+                    w.chain += chain_base;
+                }
+            chain_base += top;
+            from_.push_back({i, r.size()});
+            req.insert(req.end(), r.begin(), r.end());
+            any = true;
+        }
+        if (any) return true;
+        found.clear();
+        evals = 0;
+        cost = 0.0;
+        for (const auto &m : subs_) {
+            found.insert(found.end(), m->found.begin(), m->found.end());
+            evals += m->evals;
+            cost += m->cost;
+        }
+        std::stable_sort(found.begin(), found.end(),
+                         [](const isycos_result_window &u, const isycos_result_window &v) { return u.t_s < v.t_s; });
+        return false;
+    }
+
+    void give(const isycos_mi_out *res, size_t n) override {
+        size_t off = 0;
+        for (const auto &f : from_) {
+            subs_[f.first]->give(res + off, f.second);
+            off += f.second;
+        }
+        (void)n;
+    }
+
+    void init() {
+        const int64_t N = t_end - t_begin;
+        const int64_t L = std::max<int64_t>(1, N / prm.chunks);
+        SearchParams p = prm;
+        p.chunks = 1;
+        for (int64_t i = 0; i < N; i += L) {
+            const int64_t a = t_begin + std::max<int64_t>(0, i - prm.s_max);
+            const int64_t b = t_begin + std::min<int64_t>(N, i + L);
+            subs_.push_back(make_machine(xs, ys, a, b, p));
+        }
+        done_.assign(subs_.size(), false);
+    }
+
+private:
+    std::vector<std::unique_ptr<SearchMachine>> subs_;
+    std::vector<bool> done_;
+    std::vector<std::pair<size_t, size_t>> from_;
+};
+
 }  // namespace
 
 std::unique_ptr<SearchMachine> make_machine(int32_t xs, int32_t ys, int64_t t_begin, int64_t t_end,
                                             const SearchParams &p) {
+    if (p.chunks > 1 && p.mode != 2) {
+        auto m = std::make_unique<ChunkMachine>();
+        m->xs = xs;
+        m->ys = ys;
+        m->t_begin = t_begin;
+        m->t_end = t_end;
+        m->prm = p;
+        m->init();
+        return m;
+    }
     if (p.mode == 2) {
         auto m = std::make_unique<SelectMachine>();
         m->xs = xs;
@@ -797,65 +996,78 @@ double scratch_cost(const std::vector<const WinReq *> &g) {
 
 }  // namespace
 
-isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
-                            std::vector<bool> &finished, cudaStream_t st, int64_t *n_eval) {
-    thread_local std::vector<std::vector<WinReq>> reqs;
-    if (reqs.size() < ms.size()) reqs.resize(ms.size());
-    for (size_t q = 0; q < ms.size(); ++q) reqs[q].clear();
-    thread_local std::vector<size_t> first;
-    first.assign(ms.size(), 0);
+// Machines are batched together when they share k and the estimator.
+constexpr int kBatchKeys = 2 * (kMaxK + 1);
+inline int batch_key(const SearchMachine &m) { return m.prm.k + (kMaxK + 1) * m.prm.estimator; }
+
+// Collect the machines' requests and start their evaluation on lane L: chains (rare) run
+// synchronously, batched windows of every k but the last too, and the last batch is left
+// open on the lane; round_end() waits for it and hands the results to the machines.
+isycos_status round_begin(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
+                          std::vector<bool> &finished, cudaStream_t st, Round &rd) {
+    rd.ms = &ms;
+    rd.finished = &finished;
+    rd.L = &L;
+    rd.open_k = 0;
+    if (rd.reqs.size() < ms.size()) rd.reqs.resize(ms.size());
+    for (size_t q = 0; q < ms.size(); ++q) rd.reqs[q].clear();
+    rd.first.assign(ms.size(), 0);
+    rd.active.assign(ms.size(), 0);
     size_t total = 0;
     int k = 0;
-    thread_local std::vector<char> active_tl;
-    std::vector<char> &active = active_tl;
-    std::vector<std::vector<WinReq>> &rq_all = reqs;
-    active.assign(ms.size(), 0);
     for (size_t q = 0; q < ms.size(); ++q)
-        if (!finished[q]) active[q] = ms[q]->want(rq_all[q]) ? 1 : 0;
+        if (!finished[q]) rd.active[q] = ms[q]->want(rd.reqs[q]) ? 1 : 0;
     for (size_t q = 0; q < ms.size(); ++q) {
         if (finished[q]) continue;
-        if (!active[q]) {
+        if (!rd.active[q]) {
             finished[q] = true;
             continue;
         }
-        if (k && ms[q]->prm.k != k) k = -1;
-        if (k == 0) k = ms[q]->prm.k;
-        first[q] = total;
-        total += reqs[q].size();
+        if (k && batch_key(*ms[q]) != k) k = -1;
+        if (k == 0) k = batch_key(*ms[q]);
+        rd.first[q] = total;
+        total += rd.reqs[q].size();
     }
-    if (n_eval) *n_eval = (int64_t)total;
+    rd.total = total;
     if (total == 0) return ISYCOS_OK;
-    thread_local std::vector<isycos_mi_out> res;
-    res.resize(total);
-    // Per k (machines of one call normally share it), split the requests into the batched
-    // list and the chains that the incremental kernel takes.
-    for (int kk = 1; kk <= kMaxK; ++kk) {
+    rd.res.resize(total);
+    int last_k = 0;
+    for (int kk = 1; kk < kBatchKeys; ++kk)
+        for (size_t q = 0; q < ms.size(); ++q)
+            if (!finished[q] && !rd.reqs[q].empty() && batch_key(*ms[q]) == kk) last_k = kk;
+    // Per (k, estimator) (machines of one call normally share them), split the requests into
+    // the batched list and the chains that the incremental kernel takes.
+    for (int kk = 1; kk < kBatchKeys; ++kk) {
         if (k > 0 && kk != k) continue;
-        std::vector<HostWindow> batch;
-        std::vector<size_t> where;
+        const int k_nb = kk % (kMaxK + 1), est = kk / (kMaxK + 1);
+        std::vector<HostWindow> &batch = rd.batch;
+        std::vector<size_t> &where = rd.where;
+        batch.clear();
+        where.clear();
         std::vector<ChainSpec> chains;
         for (size_t q = 0; q < ms.size(); ++q) {
-            if (finished[q] || reqs[q].empty() || ms[q]->prm.k != kk) continue;
-            const auto &rq = reqs[q];
+            if (finished[q] || rd.reqs[q].empty() || batch_key(*ms[q]) != kk) continue;
+            const auto &rq = rd.reqs[q];
             int32_t n_groups = 0;
             for (const WinReq &r : rq) n_groups = std::max(n_groups, r.chain + 1);
             thread_local std::vector<char> in_chain;
             in_chain.assign(rq.size(), 0);
-            if (ctx->opt_incremental == 0) n_groups = 0;
+            // the incremental kernel implements the second estimator only
+            if (ctx->opt_incremental == 0 || est != 0) n_groups = 0;
             thread_local std::vector<std::vector<size_t>> groups;
             if (groups.size() < (size_t)n_groups) groups.resize((size_t)n_groups);
             for (int32_t gi = 0; gi < n_groups; ++gi) groups[gi].clear();
             for (size_t i = 0; i < rq.size(); ++i)
                 if (rq[i].chain >= 0 && rq[i].chain < n_groups) groups[rq[i].chain].push_back(i);
+            thread_local std::vector<const WinReq *> g;
             for (int32_t gi = 0; gi < n_groups; ++gi) {
                 const std::vector<size_t> &members = groups[gi];
                 if (members.size() < 2) continue;
-                std::vector<const WinReq *> g;
+                g.clear();
                 for (size_t i : members) g.push_back(&rq[i]);
                 bool use = false;
-                if (g.size() >= 2 && ctx->opt_incremental == 2) use = true;
-                if (g.size() >= 2 && ctx->opt_incremental == 1)
-                    use = chain_cost(g, kk) < 0.5 * scratch_cost(g);
+                if (ctx->opt_incremental == 2) use = true;
+                if (ctx->opt_incremental == 1) use = chain_cost(g, k_nb) < 0.5 * scratch_cost(g);
                 if (!use) continue;
                 ChainSpec sp;
                 sp.xs = ms[q]->xs;
@@ -863,7 +1075,7 @@ isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine 
                 for (size_t i : members) {
                     sp.starts.push_back(rq[i].start);
                     sp.sizes.push_back(rq[i].m);
-                    sp.out_idx.push_back(rq[i].base ? -1 : (int64_t)(first[q] + i));
+                    sp.out_idx.push_back(rq[i].base ? -1 : (int64_t)(rd.first[q] + i));
                     in_chain[i] = 1;
                 }
                 chains.push_back(std::move(sp));
@@ -871,27 +1083,52 @@ isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine 
             for (size_t i = 0; i < rq.size(); ++i) {
                 if (in_chain[i] || rq[i].base) continue;
                 batch.push_back(HostWindow{ms[q]->xs, ms[q]->ys, rq[i].start, rq[i].m});
-                where.push_back(first[q] + i);
+                where.push_back(rd.first[q] + i);
             }
         }
-        if (!batch.empty()) {
-            std::vector<isycos_mi_out> r2(batch.size());
-            isycos_status rc = engine_eval(ctx, L, batch.data(), (int64_t)batch.size(), kk, r2.data(),
-                                           nullptr, nullptr, nullptr, st);
-            if (rc) return rc;
-            for (size_t i = 0; i < batch.size(); ++i) res[where[i]] = r2[i];
-        }
         if (!chains.empty()) {
-            isycos_status rc = engine_eval_chains(ctx, L, chains.data(), chains.size(), kk, res.data(),
+            isycos_status rc = engine_eval_chains(ctx, L, chains.data(), chains.size(), k_nb, rd.res.data(),
                                                   (int64_t)total, st);
             if (rc) return rc;
         }
+        if (!batch.empty()) {
+            isycos_status rc = engine_launch(ctx, L, batch.data(), (int64_t)batch.size(), k_nb, est,
+                                             nullptr, nullptr, nullptr, st);
+            if (rc) return rc;
+            if (kk == last_k) {
+                rd.open_k = kk;   // left open for round_end
+            } else {
+                rd.tmp.resize(batch.size());
+                if ((rc = engine_collect(ctx, L, rd.tmp.data()))) return rc;
+                for (size_t i = 0; i < batch.size(); ++i) rd.res[where[i]] = rd.tmp[i];
+            }
+        }
     }
-    std::vector<isycos_mi_out> &res_all = res;
-    std::vector<size_t> &first_all = first;
-    for (size_t q = 0; q < ms.size(); ++q)
-        if (!finished[q] && !rq_all[q].empty()) ms[q]->give(res_all.data() + first_all[q], rq_all[q].size());
     return ISYCOS_OK;
+}
+
+isycos_status round_end(isycos_ctx *ctx, Round &rd) {
+    if (rd.total == 0) return ISYCOS_OK;
+    if (rd.open_k) {
+        rd.tmp.resize(rd.batch.size());
+        isycos_status rc = engine_collect(ctx, *rd.L, rd.tmp.data());
+        rd.open_k = 0;
+        if (rc) return rc;
+        for (size_t i = 0; i < rd.batch.size(); ++i) rd.res[rd.where[i]] = rd.tmp[i];
+    }
+    std::vector<SearchMachine *> &ms = *rd.ms;
+    for (size_t q = 0; q < ms.size(); ++q)
+        if (!(*rd.finished)[q] && !rd.reqs[q].empty()) ms[q]->give(rd.res.data() + rd.first[q], rd.reqs[q].size());
+    return ISYCOS_OK;
+}
+
+isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
+                            std::vector<bool> &finished, cudaStream_t st, int64_t *n_eval) {
+    thread_local Round rd;
+    isycos_status rc = round_begin(ctx, L, ms, finished, st, rd);
+    if (n_eval) *n_eval = (int64_t)rd.total;
+    if (rc) return rc;
+    return round_end(ctx, rd);
 }
 
 isycos_status run_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
@@ -906,6 +1143,7 @@ isycos_status run_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *
         if (all) return ISYCOS_OK;
     }
 }
+
 }  // namespace isy
 
 using namespace isy;

@@ -25,6 +25,8 @@ struct SearchParams {
     uint64_t seed;
     int sel_partitions, sel_samples;   // Algorithm 3
     double sel_alpha, sel_rho;
+    int chunks;                        // Algorithm 4 (<= 1: unchunked)
+    int estimator;                     // 0: KSG estimator 2, 1: KSG estimator 1
 };
 
 isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchParams *out);
@@ -149,5 +151,25 @@ isycos_status run_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *
 // Returns the number of windows evaluated.  Caller holds ctx->engine_mu.
 isycos_status step_machines(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
                             std::vector<bool> &finished, cudaStream_t st, int64_t *n_eval);
+
+// A round split in two: round_begin collects the requests and launches their batch on lane
+// L (asynchronously), round_end waits for it and delivers the results.
+struct Round {
+    std::vector<SearchMachine *> *ms = nullptr;
+    std::vector<bool> *finished = nullptr;
+    Lane *L = nullptr;
+    std::vector<std::vector<WinReq>> reqs;
+    std::vector<size_t> first;
+    std::vector<char> active;
+    size_t total = 0;
+    std::vector<isycos_mi_out> res, tmp;
+    std::vector<HostWindow> batch;
+    std::vector<size_t> where;
+    int open_k = 0;
+};
+isycos_status round_begin(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *> &ms,
+                          std::vector<bool> &finished, cudaStream_t st, Round &rd);
+isycos_status round_end(isycos_ctx *ctx, Round &rd);
+
 
 }  // namespace isy

@@ -13,7 +13,11 @@ does not come from the oracle itself:
 - ``pin_entropy``: the plug-in joint entropy against SciPy's entropy of the cell counts;
 - ``pin_invariants``: symmetry, sign and power-of-two scale invariance, bit for bit;
 - ``pin_gaussian``: the bivariate-Gaussian closed form -1/2 ln(1 - rho^2) within the
-  estimator's sampling error.
+  estimator's sampling error;
+- ``pin_est1_*``: the same kinds of pins for Kraskov's first estimator (strict counts in
+  strips of half-width eps_i, psi(n + 1), no -1/k): a hand-worked window, the NumPy brute
+  force, and the closed form Y = X, where every count is k - 1 and the estimate is
+  psi(m) - psi(k).
 
 The same functions run against planted mistakes of the oracle (tests/test_oracle_mutations.py)
 to show that each plausible mistake fails at least one pin.
@@ -59,6 +63,27 @@ def numpy_ksg(x, y, k):
     mi = digamma(k) - 1.0 / k - np.mean(digamma(nx) + digamma(ny)) + digamma(m)
     h = math.log(m) - np.mean(np.log(c))
     return nx, ny, c, mi, h
+
+
+def numpy_ksg1(x, y, k):
+    """Kraskov's first estimator by brute force: eps_i = k-th smallest max-norm distance to
+    the other points, n_x = #{j != i : |x_i - x_j| < eps_i}, psi(k) + psi(m) - <psi(n_x + 1)
+    + psi(n_y + 1)>."""
+    x = np.asarray(x, dtype=np.float32)
+    y = np.asarray(y, dtype=np.float32)
+    m = x.shape[0]
+    ax = np.abs(x[:, None] - x[None, :])
+    ay = np.abs(y[:, None] - y[None, :])
+    d = np.maximum(ax, ay)
+    nx = np.empty(m, dtype=np.int64)
+    ny = np.empty(m, dtype=np.int64)
+    for i in range(m):
+        others = np.delete(np.arange(m), i)
+        eps = np.sort(d[i, others])[k - 1]
+        nx[i] = int(np.sum(ax[i, others] < eps))
+        ny[i] = int(np.sum(ay[i, others] < eps))
+    mi = digamma(k) + digamma(m) - np.mean(digamma(nx + 1) + digamma(ny + 1))
+    return nx, ny, mi
 
 
 # ---------------------------------------------------------------------------
@@ -201,12 +226,12 @@ def pin_invariants():
         assert r["s_psi"] == base["s_psi"]
 
 
-def pin_gaussian(windows=24, m=256):
+def pin_gaussian(windows=24, m=256, estimator=0):
     for t, rho in enumerate([0.0, 0.6, 0.9]):
         vals = []
         for w in range(windows):
             x, y = synth.gaussian_pair(synth.seed_for(94, t, w), m, rho)
-            vals.append(O.ksg_window(x, y, 4, points=False)["mi_exact"])
+            vals.append(O.ksg_window(x, y, 4, points=False, estimator=estimator)["mi_exact"])
         vals = np.array(vals)
         truth = -0.5 * math.log(1.0 - rho * rho)
         se = vals.std(ddof=1) / math.sqrt(len(vals))
@@ -214,5 +239,51 @@ def pin_gaussian(windows=24, m=256):
         assert abs(vals.mean() - truth) < 4.0 * se + 0.03, (rho, vals.mean(), truth, se)
 
 
+def pin_est1_hand_window():
+    # The window of pin_hand_window, k = 1, Kraskov's first estimator:
+    # p0: eps=1 (p1); |dx|<1: none -> n_x=0; |dy|<1: p1 (.5), p2 (0) -> n_y=2
+    # p1: eps=1 (p0); |dx|<1: none -> 0;      |dy|<1: p0 (.5), p2 (.5) -> 2
+    # p2: eps=2 (p1, p3); |dx|<2: p3 (.5) -> 1 (p1 at exactly 2 is out); |dy|<2: p0, p1 -> 2
+    # p3: eps=2 (p2); |dx|<2: p2 (.5) -> 1;   |dy|<2: p1 (1.5) -> 1
+    x = np.array([0.0, 1.0, 3.0, 3.5], dtype=np.float32)
+    y = np.array([0.0, 0.5, 0.0, 2.0], dtype=np.float32)
+    r = O.ksg_window(x, y, 1, estimator=1)
+    assert list(r["nx"]) == [0, 0, 1, 1], r["nx"]
+    assert list(r["ny"]) == [2, 2, 2, 1], r["ny"]
+    mi = digamma(1) + digamma(4) - (
+        2 * (digamma(1) + digamma(3)) + (digamma(2) + digamma(3)) + (digamma(2) + digamma(2))) / 4
+    assert abs(r["mi_exact"] - mi) < 1e-12, (r["mi_exact"], mi)
+    assert abs(r["mi"] - mi) < 1e-8, (r["mi"], mi)
+
+
+def pin_est1_brute_force():
+    for x, y, k in _small_cases():
+        nx, ny, mi = numpy_ksg1(x, y, k)
+        r = O.ksg_window(x, y, k, estimator=1)
+        assert np.array_equal(r["nx"], nx), (k, r["nx"], nx)
+        assert np.array_equal(r["ny"], ny), (k, r["ny"], ny)
+        assert abs(r["mi_exact"] - mi) < 1e-10, (r["mi_exact"], mi)
+        assert abs(r["mi"] - mi) < 1e-8, (r["mi"], mi)
+        base = O.ksg_window(x, y, k)
+        assert np.array_equal(r["c"], base["c"]) and r["h_w"] == base["h_w"]
+
+
+def pin_est1_closed_form():
+    for t, (m, k) in enumerate([(32, 4), (64, 3), (128, 6), (257, 4), (40, 1)]):
+        x = synth.normal(synth.seed_for(91, t), m).astype(np.float32)
+        assert _tie_free_line(x, k)
+        expect = digamma(m) - digamma(k)
+        # (the strips have the same half-width in both dimensions, so unlike the second
+        # estimator a scaled Y = 2^s X does not reduce to the closed form)
+        for y in (x.copy(), -x):
+            r = O.ksg_window(x, y, k, estimator=1)
+            assert np.all(r["nx"] == k - 1) and np.all(r["ny"] == k - 1), (r["nx"], r["ny"])
+            assert abs(r["mi_exact"] - expect) < 1e-11, (r["mi_exact"], expect)
+            assert abs(r["mi"] - expect) < 1e-8, (r["mi"], expect)
+            sym = O.ksg_window(y, x, k, estimator=1)
+            assert sym["mi"] == r["mi"]
+
+
 FAST_PINS = [pin_paper_example, pin_hand_window, pin_brute_force, pin_closed_form,
-             pin_entropy, pin_invariants]
+             pin_entropy, pin_invariants, pin_est1_hand_window, pin_est1_brute_force,
+             pin_est1_closed_form]

@@ -45,7 +45,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(api.isycos_window) == 24
     assert ctypes.sizeof(api.isycos_mi_out) == 40
     assert ctypes.sizeof(api.isycos_result_window) == 32
-    assert ctypes.sizeof(api.isycos_params) == 96
+    assert ctypes.sizeof(api.isycos_params) == 104
     assert ctypes.sizeof(api.isycos_stats) == 440
 
 

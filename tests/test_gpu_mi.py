@@ -261,3 +261,88 @@ def test_sorted_path_equals_brute_force(ctx):
             assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
         api.isycos_drop_series(ctx, xs)
         api.isycos_drop_series(ctx, ys)
+
+
+def _check_points_est1(ctx, x, y, starts, sizes, k):
+    api = _api()
+    xs = api.isycos_put_series(ctx, x)
+    ys = api.isycos_put_series(ctx, y)
+    w = api.windows_array(xs, ys, starts, sizes)
+    api.isycos_set_option(ctx, api.OPT_ESTIMATOR, 1)
+    try:
+        out, nx, ny, c = api.isycos_mi_windows_points(ctx, w, k)
+        out2 = api.isycos_mi_windows(ctx, w, k)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_ESTIMATOR, 0)
+    off = 0
+    for i, (s, m) in enumerate(zip(starts, sizes)):
+        r = O.ksg_window(x[s:s + m], y[s:s + m], k, estimator=1)
+        assert np.array_equal(nx[off:off + m], r["nx"]), (m, k, "nx")
+        assert np.array_equal(ny[off:off + m], r["ny"]), (m, k, "ny")
+        assert np.array_equal(c[off:off + m], r["c"]), (m, k, "c")
+        assert out["s_psi"][i] == r["s_psi"] and out["s_log"][i] == r["s_log"], (m, k)
+        assert abs(out["mi"][i] - r["mi"]) <= TOL and abs(out["nmi"][i] - r["nmi"]) <= TOL
+        off += m
+    assert np.array_equal(out2["s_psi"], out["s_psi"]) and np.array_equal(out2["mi"], out["mi"])
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+
+
+@pytest.mark.parametrize("k", [1, 3, 4, 8])
+def test_estimator1_points_bucket_edges(ctx, k):
+    """Kraskov's first estimator (strict counts in strips of half-width eps_i, psi(n + 1),
+    no -1/k) on the warp path (m <= 64) and the CTA path, against the oracle per point."""
+    x, y, _ = synth.planted_pair(5, k, 6000)
+    sizes = [k + 1, 31, 32, 33, 64, 65, 127, 257, 700, 1024]
+    starts = [(37 * i) % (6000 - 1100) for i in range(len(sizes))]
+    _check_points_est1(ctx, x, y, starts, sizes, k)
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_estimator1_heavy_ties(ctx, k):
+    x, y, _ = synth.planted_pair(5, 10 + k, 4000)
+    xq, yq = synth.quantize(x, 2.0), synth.quantize(y, 2.0)
+    sizes = [20, 64, 200, 513]
+    starts = [5, 300, 900, 2000]
+    _check_points_est1(ctx, xq, yq, starts, sizes, k)
+    dup = np.array([1, 1, 1, 1, 1, 1, 2, 2, 3], np.float32)
+    _check_points_est1(ctx, dup, dup[::-1].copy(), [0], [9], 3)
+
+
+def test_estimator1_sorted_plain_and_device_paths(ctx):
+    """The sorted-strip path (1025..4096 points), the one-window-per-launch path and the
+    device-list path give the same estimator-1 results as the brute-force path."""
+    import torch
+    api = _api()
+    n = 12000
+    x, y, _ = synth.planted_pair(8, 3, n)
+    for xx, yy in ((x, y), (synth.quantize(x), synth.quantize(y))):
+        xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
+        sizes = [1025, 2048, 4096, 300]
+        starts = [10, 2000, 5000, 9500]
+        w = api.windows_array(xs, ys, starts, sizes)
+        api.isycos_set_option(ctx, api.OPT_ESTIMATOR, 1)
+        res = {}
+        try:
+            for opt in (1, 2):
+                api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+                res[opt] = api.isycos_mi_windows_points(ctx, w, 4)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+            plain = api.isycos_mi_windows_plain(ctx, w, 4)
+            dw = torch.from_numpy(w.view(np.uint8)).cuda()
+            dout = torch.empty(len(w) * 40, dtype=torch.uint8, device="cuda")
+            st = torch.cuda.current_stream()
+            api.isycos_mi_windows_device(ctx, dw, len(w), 4, 4096, dout, st)
+            api.isycos_device_status(ctx, st)
+            dev = dout.cpu().numpy().view(api.MI_OUT_DTYPE)
+        finally:
+            api.isycos_set_option(ctx, api.OPT_ESTIMATOR, 0)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+        for a, b in zip(res[1], res[2]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(plain["s_psi"], res[1][0]["s_psi"])
+        assert np.array_equal(dev["s_psi"], res[1][0]["s_psi"]) and np.array_equal(dev["mi"], res[1][0]["mi"])
+        r = O.ksg_window(xx[2000:4048], yy[2000:4048], 4, points=False, estimator=1)
+        assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
+        api.isycos_drop_series(ctx, xs)
+        api.isycos_drop_series(ctx, ys)

@@ -309,3 +309,56 @@ def test_selection_matches_oracle(ctx, case):
     ref, n, sel, _ = O.search_auto(x, y, partitions=8, samples=3, **kw)
     _same(got, ref)
     assert st["decided_windows"] == n
+
+
+@pytest.mark.parametrize("extra", [dict(mode=0, chunks=4), dict(mode=1, chunks=3, pruning=1),
+                                   dict(mode=0, chunks=7, pruning=1, s_max=128),
+                                   dict(mode=2, chunks=3, sel_partitions=8, sel_samples=3)],
+                         ids=lambda d: ",".join("%s=%s" % kv for kv in d.items()))
+def test_chunked_search_matches_oracle(ctx, extra):
+    """Algorithm 4: the range is searched as overlapping chunks; the GPU's chunk searches run
+    batched together and must return the oracle's concatenated, t_s-sorted windows and its
+    evaluation count."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, seed=9)
+    kw.update(extra)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    api.isycos_reset_stats(ctx)
+    got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+    st = api.isycos_get_stats(ctx)
+    okw = dict(kw)
+    mode = okw.pop("mode")
+    if mode == 2:
+        ref, n, _, _ = O.search_auto(x, y, partitions=okw.pop("sel_partitions"),
+                                     samples=okw.pop("sel_samples"), **okw)
+    else:
+        ref, n = O.search_chunked(x, y, mode=mode, **okw)
+    _same(got, ref)
+    assert st["decided_windows"] == n
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+
+
+@pytest.mark.parametrize("extra", [dict(mode=0, pruning=1), dict(mode=1, pruning=1),
+                                   dict(mode=1, pruning=0, chunks=3)],
+                         ids=lambda d: ",".join("%s=%s" % kv for kv in d.items()))
+def test_search_with_estimator1_matches_oracle(ctx, extra):
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, seed=13, estimator=1)
+    kw.update(extra)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    api.isycos_reset_stats(ctx)
+    got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+    st = api.isycos_get_stats(ctx)
+    okw = dict(kw)
+    mode = okw.pop("mode")
+    if "chunks" in okw:
+        ref, n = O.search_chunked(x, y, mode=mode, **okw)
+    else:
+        ref, n = (O.search_td if mode == 0 else O.search_bu)(x, y, **okw)
+    _same(got, ref)
+    assert st["decided_windows"] == n
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)

@@ -34,8 +34,9 @@ def test_fast_pin(pin):
     pin()
 
 
-def test_gaussian_closed_form_and_independence():
-    _pins.pin_gaussian()
+@pytest.mark.parametrize("estimator", [0, 1])
+def test_gaussian_closed_form_and_independence(estimator):
+    _pins.pin_gaussian(estimator=estimator)
 
 
 def test_gaussian_large_window():

@@ -123,3 +123,44 @@ def test_selection_runs_the_selected_search(seed):
     ref, _ = (O.search_td if sel == 0 else O.search_bu)(x, y, **kw)
     assert [(a, b) for a, b, _, _ in wins] == [(a, b) for a, b, _, _ in ref]
     assert n > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chunked_search_with_one_chunk_is_the_plain_search(mode):
+    """Algorithm 4 with n_p = 1 is the unchunked search (a single chunk [0, N))."""
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, pruning=1, seed=3)
+    plain = (O.search_td if mode == 0 else O.search_bu)(x, y, **kw)
+    assert O.search_chunked(x, y, mode=mode, chunks=1, **kw) == plain
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chunked_search_recovers_the_planted_segments(mode):
+    """Chunks overlap by s_max, so segments that cross a chunk boundary are still found:
+    with 4 chunks of 500 points the boundaries at 500 and 1500 cut both planted segments
+    ([400, 700) and [1200, 1500)), and windows overlapping each are still returned."""
+    x, y = synth.planted_small_pair()
+    wins, _ = O.search_chunked(x, y, mode=mode, chunks=4, k=4, s_min=32, s_max=256, pruning=0)
+    assert [w[0] for w in wins] == sorted(w[0] for w in wins)
+    for lo, hi in ((400, 700), (1200, 1500)):
+        assert any(a < hi and b >= lo for a, b, _, _ in wins), (lo, hi, wins)
+    for a, b, sc, _ in wins:
+        assert 0 <= a < b < len(x) and sc >= 0.2 and 32 <= b - a + 1 <= 256
+
+
+def test_chunked_search_windows_lie_in_their_chunks():
+    """Every returned window lies inside one chunk [i L - s_max, (i + 1) L) and no chunk's
+    windows overlap each other (each chunk is a plain search); a mocked score that is high on
+    one block only, far from the boundaries, gives exactly the unchunked windows."""
+    def score(ts, te):
+        inside = 300 <= ts and te < 500
+        return (0.9 if inside else 0.0), 0.0
+    N, chunks, s_max = 4000, 4, 128
+    plain, _ = O.search_td(score, None, 0, N, k=4, s_min=32, s_max=s_max)
+    chunked, _ = O.search_chunked(score, None, 0, N, mode=0, chunks=chunks, k=4, s_min=32, s_max=s_max)
+    assert chunked == plain and plain
+    L = N // chunks
+    wins, _ = O.search_chunked(*synth.planted_small_pair(), mode=1, chunks=chunks, k=4,
+                               s_min=32, s_max=s_max)
+    for a, b, _, _ in wins:
+        assert any(max(0, i - s_max) <= a and b < min(N, i + L) for i in range(0, N, L))
