@@ -3,10 +3,11 @@
 Workload (one "step"): the paper's searches over 64 synthetic pairs of FP32 series of length
 100,000 with planted linear / quadratic / sin(3X) / exp(X) segments (lengths log-uniform in
 [50, 5000], SNR in {0.5, 2, 10}, iid N(0,1) background), k = 4, window sizes 32-4096,
-sigma = 0.2 on the normalised score, noise pruning on: SYCOS_TD (Algorithm 1) and SYCOS_BU
-(Algorithm 2) over all 64 pairs, each algorithm's frontiers of all pairs merged into shared
-persistent MI launches.  The series stay resident in HBM (value); the e2e figure uploads them
-from pinned host memory and reads the found windows back inside the timed region.
+sigma = 0.2 on the normalised score, noise pruning on: a SYCOS_TD (Algorithm 1) and a
+SYCOS_BU (Algorithm 2) query per pair, 128 queries run concurrently on the library's engine
+lanes, each lane merging its queries' window frontiers into persistent, size-bucketed MI
+launches.  The series stay resident in HBM (value); the e2e figure uploads them from pinned
+host memory and reads the found windows back inside the timed region.
 
 The JSON line follows the driver's contract; see the design doc for the roofline definition.
 """
@@ -50,6 +51,12 @@ def parse():
                     help="time one MI batch instead of the searches: td4096, td1024, td256, "
                          "ring (BU-ring sized windows), mix (all TD layers)")
     ap.add_argument("--case-pairs", type=int, default=8)
+    ap.add_argument("--search-case", default=None, choices=["td", "bu", "mix", "select", "chunked"],
+                    help="time one kind of search query over --case-pairs pairs of --length "
+                         "points instead of the default step (per-size launch statistics)")
+    ap.add_argument("--lanes", type=int, default=0, help="ISYCOS_OPT_LANES (0: library default)")
+    ap.add_argument("--speculation", type=int, default=-1,
+                    help="ISYCOS_OPT_SPECULATION (BU climbs asked ahead; -1: library default)")
     ap.add_argument("--plain", action="store_true", help="also time the one-window-per-launch form")
     ap.add_argument("--kernel-opt", type=int, default=0,
                     help="ISYCOS_OPT_KERNEL: 0 auto, 1 brute force only, 2 sorted path")
@@ -326,8 +333,51 @@ def kernel_case(args):
     api.isycos_destroy(ctx)
 
 
+def search_case(args):
+    """Searches of one kind over a few pairs: time per pass and the library's per-size
+    launch statistics (windows, launches and summed launch time by window-size bucket)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api
+    pairs = make_pairs(0, args.case_pairs, args.length)
+    ctx = api.isycos_create(0, 0)
+    if args.lanes:
+        api.isycos_set_option(ctx, api.OPT_LANES, args.lanes)
+    if args.speculation >= 0:
+        api.isycos_set_option(ctx, api.OPT_SPECULATION, args.speculation)
+    ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
+    extra = {"td": [dict(mode=0)], "bu": [dict(mode=1)], "mix": [dict(mode=0), dict(mode=1)],
+             "select": [dict(mode=2)], "chunked": [dict(mode=1, chunks=8)]}[args.search_case]
+    qs = [(a, b, 0, args.length, dict(PARAMS, **e)) for e in extra for a, b in ids]
+    for _ in range(args.warmup):
+        api.isycos_search_queries(ctx, qs)
+    torch.cuda.synchronize()
+    api.isycos_reset_stats(ctx)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        api.isycos_search_queries(ctx, qs)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    st = api.isycos_get_stats(ctx)
+    k = args.steps
+    line = {"search_case": args.search_case, "pairs": args.case_pairs, "length": args.length,
+            "lanes": args.lanes, "speculation": args.speculation,
+            "s_per_pass": round(dt, 4), "decided_windows": st["decided_windows"] // k,
+            "gpu_windows": st["windows"] // k, "launches": st["launches"] // k,
+            "kernel_ms": round(st["mi_kernel_ms"] / k, 2),
+            "windows_by_size": [v // k for v in st["windows_by_size"]],
+            "launches_by_size": [v // k for v in st["launches_by_size"]],
+            "launch_ms_by_size": [round(v / k, 2) for v in st["launch_ms_by_size"]]}
+    print(json.dumps(line), flush=True)
+    api.isycos_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.search_case:
+        return search_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.kernel_case:
@@ -349,6 +399,8 @@ def main():
     ctx = api.isycos_create(local, 0)
     ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
     l2buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    # per-bucket choice between the brute-force and sorted MI paths, timed on this GPU
+    tune = api.isycos_autotune(ctx, PARAMS["k"])
 
     for _ in range(args.warmup):
         run_step(api, ctx, ids, args.length)
@@ -432,6 +484,24 @@ def main():
     if rank == 0 and not args.no_serving:
         serving = serving_probe(api, ctx, ids, args.length)
 
+    # the plain form (one window per launch) against the batched form, on 2,000 windows shaped
+    # like the BU rings of the step (32-1024 points)
+    plain = None
+    if rank == 0:
+        wr = case_windows("ring", ids[:1], args.length, np.random.default_rng(5))
+        api.isycos_mi_windows(ctx, wr, PARAMS["k"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp = api.isycos_mi_windows_plain(ctx, wr, PARAMS["k"])
+        t_plain = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rb = api.isycos_mi_windows(ctx, wr, PARAMS["k"])
+        t_batch = time.perf_counter() - t0
+        plain = {"windows": int(len(wr)), "plain_evals_per_s": round(len(wr) / t_plain, 1),
+                 "batched_evals_per_s": round(len(wr) / t_batch, 1),
+                 "speedup": round(t_plain / t_batch, 1),
+                 "same_results": bool(np.array_equal(rp["s_psi"], rb["s_psi"]))}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pairs)
@@ -446,7 +516,10 @@ def main():
                        "length": args.length, "k": 4, "s_min": 32, "s_max": 4096,
                        "sigma": 0.2, "pruning": 1,
                        "searches": "SYCOS_TD and SYCOS_BU queries of every pair, concurrently",
-                       "l2": "flushed between timed steps (256 MiB write)"},
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "autotune": {"sorted_buckets": tune["sorted_buckets"],
+                                    "window_size": tune["window_size"],
+                                    "brute_ms": tune["brute_ms"], "sorted_ms": tune["sorted_ms"]}},
             "pairs_per_s": round(pairs_per_s, 1),
             "pairs_note": "brute-force-equivalent ordered pairs m(m-1) per evaluated window",
             "windows_per_step": int(windows_all / args.steps),
@@ -456,6 +529,7 @@ def main():
             "incremental_windows_per_step": int(st["incr_windows"] / args.steps),
             "gpu_launches": int(st["launches"]),
             "roofline": roof, "clocks": clocks, "e2e": e2e, "serving": serving,
+            "plain_vs_batched": plain,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

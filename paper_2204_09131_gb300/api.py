@@ -33,6 +33,7 @@ OPT_SERVE_SLOTS = 3
 OPT_SERVE_QUEUE = 4
 OPT_LANES = 5
 OPT_ESTIMATOR = 6
+OPT_SPECULATION = 7
 
 
 class IsycosError(RuntimeError):
@@ -61,6 +62,12 @@ class isycos_params(ctypes.Structure):
                 ("sel_samples", ctypes.c_int32), ("sel_alpha", ctypes.c_double),
                 ("sel_rho", ctypes.c_double), ("chunks", ctypes.c_int32),
                 ("estimator", ctypes.c_int32)]
+
+
+class isycos_tuning(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("sorted_buckets", ctypes.c_uint32),
+                ("window_size", ctypes.c_int32 * 15), ("n_windows", ctypes.c_int32),
+                ("brute_ms", ctypes.c_double * 15), ("sorted_ms", ctypes.c_double * 15)]
 
 
 class isycos_query(ctypes.Structure):
@@ -127,6 +134,7 @@ SIGNATURES = {
     "isycos_reset_stats": (_I32, [_VP]),
     "isycos_tables": (_I32, [_VP, _I32, _VP, _VP]),
     "isycos_set_option": (_I32, [_VP, _I32, _I64]),
+    "isycos_autotune": (_I32, [_VP, _I32, _VP]),
     "isycos_mi_windows_noalloc": (_I32, [_VP, _VP, _I64, _VP, _VP, _I64, _I32, _I32, _VP, _VP]),
 }
 
@@ -378,6 +386,19 @@ def isycos_tables(ctx, n_max: int):
 
 def isycos_set_option(ctx, option: int, value: int):
     return _check(ctx, lib().isycos_set_option(ctx, option, value))
+
+
+def isycos_autotune(ctx, k: int = 4) -> dict:
+    """Time the brute-force and sorted MI paths per eligible size bucket and keep the faster;
+    returns the probe sizes, times and the chosen sorted buckets."""
+    t = isycos_tuning()
+    _check(ctx, lib().isycos_autotune(ctx, k, ctypes.byref(t)))
+    buckets = [b for b in range(15) if t.window_size[b]]
+    return {"k": t.k, "n_windows": t.n_windows,
+            "sorted_buckets": [b for b in range(15) if (t.sorted_buckets >> b) & 1],
+            "window_size": {b: t.window_size[b] for b in buckets},
+            "brute_ms": {b: round(t.brute_ms[b], 4) for b in buckets},
+            "sorted_ms": {b: round(t.sorted_ms[b], 4) for b in buckets}}
 
 
 class Context:

@@ -54,7 +54,8 @@ struct BatchArgs {
     int32_t *c;
     int32_t k;
     int32_t nt;                  // threads per CTA of the launch
-    int32_t sort_min;            // windows of at least this size take the sorted path
+    uint32_t sort_mask;          // bit b set: windows of bucket b (2^(b-1) < m <= 2^b) that
+                                 // run one per CTA take the sorted path
     int32_t est;                 // 0: Kraskov's second estimator (Eq. KSGmi), 1: the first
 };
 
@@ -132,6 +133,16 @@ inline int batched_grid_need(const BucketTable &T, int nt) {
 
 // Largest window of the sorted path (its sort keys and records share the CTA's shared memory).
 constexpr int kSortMax = 4096;
+// Buckets the sorted path can take: windows of 257..4096 points, which run one per CTA (a
+// 256-thread CTA up to 1024 points, a 1024-thread CTA above); the path is used for 1025..4096
+// points unless isycos_autotune chose otherwise.
+constexpr uint32_t kSortBuckets = (1u << 9) | (1u << 10) | (1u << 11) | (1u << 12);
+constexpr uint32_t kDefaultSortBuckets = (1u << 11) | (1u << 12);
+__host__ __device__ inline int size_bucket(int m) {   // smallest b with m <= 2^b
+    int b = 0;
+    while ((1 << b) < m) ++b;
+    return b;
+}
 
 // Sorted path layout in shared memory after the window's m float2 values: the sort keys
 // (8 bytes per slot, the slot count rounded up to a power of two), the x-ordered records
@@ -152,10 +163,11 @@ inline size_t batched_smem(int max_m, int nt, int max_sorted = 0) {
     return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
-// Threads per CTA chosen for a batch whose largest window has max_m points (the sorted path
-// runs one window per CTA: more warps hide its dependent loads).
+// Threads per CTA chosen for a batch whose largest window has max_m points and whose
+// largest sorted-path window has max_sorted points (the sorted path runs one window per CTA:
+// above 1024 points it takes 1024 threads, which hide its dependent loads).
 inline int batched_threads(int max_m, int max_sorted = 0) {
-    return (max_m > 8192 || max_sorted > 0) ? 1024 : 256;
+    return (max_m > 8192 || max_sorted > 1024) ? 1024 : 256;
 }
 
 }  // namespace isy

@@ -259,6 +259,9 @@ __device__ __forceinline__ uint32_t fkey(float f) {
 
 template <int NT, typename T>
 __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all threads
+    // Element i is handled by thread i mod NT, so a step with partner distance j < 32 pairs
+    // elements of the same warp: it needs only a warp barrier before the next step, unless
+    // that next step reaches across warps.
     for (int k2 = 2; k2 <= N; k2 <<= 1)
         for (int j = k2 >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < N; i += NT) {
@@ -272,7 +275,9 @@ __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all
                     }
                 }
             }
-            __syncthreads();
+            const int jn = j > 1 ? (j >> 1) : ((k2 << 1) <= N ? k2 : 0);   // the next step's j
+            if (jn >= 32 || jn == 0) __syncthreads();
+            else __syncwarp();
         }
 }
 
@@ -322,10 +327,16 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     __syncthreads();
     bitonic_sort<NT>(ys, N);
 
-    // Phase A: the strip walks.  Lanes take points from a shared counter one at a time, so
-    // that a lane whose walk ends early starts the next point instead of idling while the
-    // rest of its warp walks on.  Per point it leaves d_x, d_y and the multiplicity (or -1
-    // when the k+1-th distance is 0 and the duplicates must be counted in phase B).
+    // Phase A: the neighbour lists, by outward scans.  A warp takes 32 consecutive points of
+    // the x order (a chunk, from a shared counter).  Every lane first scans the 64 points of
+    // the x order around the chunk, which gives its point a list of k + 1 and so a bound on
+    // its (k+1)-th distance.  The warp then extends the scanned range outward, 8 points at a
+    // time on each side, while the next point on that side is within some lane's bound in
+    // x: a point farther in x than a lane's bound cannot enter its list (d >= |dx|), and
+    // along the x order |x_i - x| only grows (binary32 rounding is monotone), while the
+    // bounds only shrink.  Every lane visits the same candidates (broadcast shared loads,
+    // warp-uniform control).  Per point it leaves d_x, d_y and the multiplicity (or -1 when
+    // the (k+1)-th distance is 0 and the duplicates must be counted in phase B).
     float *pdx = reinterpret_cast<float *>(scratch + (size_t)8 * N + (size_t)16 * m);
     float *pdy = pdx + m;
     int *pcc = reinterpret_cast<int *>(pdy + m);
@@ -333,61 +344,54 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     if (threadIdx.x == 0) *ctr = 0;
     __syncthreads();
     {
-        int state = 0;   // 0: needs a point, 1: walking, 2: no points left
-        int t = 0, lo = 0, hi = 0;
-        bool alo = false, ahi = false;
-        float xi = 0.0f, yi = 0.0f, xlo = 0.0f, xhi = 0.0f;
-        float bd[K1];
-        int bj[K1];
+        const int lane = threadIdx.x & 31;
+        const int n_chunks = (m + 31) >> 5;
         for (;;) {
-            if (state == 0) {
-                t = atomicAdd(ctr, 1);
-                if (t >= m) {
-                    state = 2;
-                } else {
-                    const float4 me = rec[t];
-                    xi = me.x;
-                    yi = me.y;
-#pragma unroll
-                    for (int r = 0; r < K1; ++r) {
-                        bd[r] = kInf;
-                        bj[r] = 0x7fffffff;
-                    }
-                    insert_lex<K1>(bd, bj, 0.0f, __float_as_int(me.z));   // the point itself
-                    lo = t - 1;
-                    hi = t + 1;
-                    alo = lo >= 0;
-                    ahi = hi < m;
-                    if (alo) xlo = rec[lo].x;
-                    if (ahi) xhi = rec[hi].x;
-                    state = 1;
-                }
+            int chunk = 0;
+            if (lane == 0) chunk = atomicAdd(ctr, 1);
+            chunk = __shfl_sync(kFull, chunk, 0);
+            if (chunk >= n_chunks) break;
+            const int c0 = chunk << 5;
+            const int t = c0 + lane;
+            const bool valid = t < m;
+            float xi = kInf, yi = kInf;
+            if (valid) {
+                const float4 me = rec[t];
+                xi = me.x;
+                yi = me.y;
             }
-            if (__all_sync(kFull, state == 2)) break;
-            if (state != 1) continue;
-            if (alo || ahi) {
-                const bool take_lo = alo && (!ahi || (xi - xlo) <= (xhi - xi));
-                const float cx = take_lo ? xlo : xhi;
-                const float ax = fabsf(xi - cx);
-                if (ax > bd[K1 - 1]) {            // nothing farther on this side can enter
-                    if (take_lo) alo = false;
-                    else ahi = false;
-                    continue;
-                }
-                const float4 c = rec[take_lo ? lo : hi];
-                const float d = fmaxf(ax, fabsf(yi - c.y));
+            float bd[K1];
+            int bj[K1];
+#pragma unroll
+            for (int r = 0; r < K1; ++r) {
+                bd[r] = kInf;
+                bj[r] = 0x7fffffff;
+            }
+            auto visit = [&](int u) {
+                const float4 c = rec[u];
+                const float d = fmaxf(fabsf(xi - c.x), fabsf(yi - c.y));
                 const int jj = __float_as_int(c.z);
                 if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
-                if (take_lo) {
-                    --lo;
-                    alo = lo >= 0;
-                    if (alo) xlo = rec[lo].x;
-                } else {
-                    ++hi;
-                    ahi = hi < m;
-                    if (ahi) xhi = rec[hi].x;
+            };
+            // the 64 points around the chunk (the point itself among them)
+            const int a0 = max(0, c0 - 16), a1 = min(m, c0 + 48);
+            for (int u = a0; u < a1; ++u) visit(u);
+            // outward, while some lane's strip reaches the next point
+            int L = a0 - 1, R = a1;
+            for (;;) {
+                const bool need_l = L >= 0 && __any_sync(kFull, valid && fabsf(xi - rec[L].x) <= bd[K1 - 1]);
+                const bool need_r = R < m && __any_sync(kFull, valid && fabsf(xi - rec[R].x) <= bd[K1 - 1]);
+                if (!need_l && !need_r) break;
+                if (need_l) {
+                    const int stop = max(L - 8, -1);
+                    for (; L > stop; --L) visit(L);
                 }
-            } else {
+                if (need_r) {
+                    const int stop = min(R + 8, m);
+                    for (; R < stop; ++R) visit(R);
+                }
+            }
+            if (valid) {
                 float dxm = 0.0f, dym = 0.0f;
                 int cc = 0;
 #pragma unroll
@@ -404,7 +408,6 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 pdx[t] = dxm;
                 pdy[t] = dym;
                 pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
-                state = 0;
             }
         }
     }
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                 nyo = a.ny + it.pts;
                 co = a.c + it.pts;
             }
-            if (per_job == 1 && it.m >= a.sort_min && it.m <= kSortMax) {
+            if (per_job == 1 && it.m <= kSortMax && ((a.sort_mask >> (32 - __clz(it.m - 1))) & 1u)) {
                 ksg_window_sorted<K1, NT>(s, it.m, reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m),
                                           a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
             } else {

@@ -224,7 +224,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     a.nx = a.ny = a.c = nullptr;
     a.k = k;
     a.nt = nt;
-    a.sort_min = INT32_MAX;   // brute-force path only
+    a.sort_mask = 0;          // brute-force path only
     a.est = 0;                // Kraskov's second estimator (Eq. KSGmi)
     if (launch_batched(a, n_sm * per_sm, smem, st) != cudaSuccess) return ISYCOS_E_CUDA;
     return ISYCOS_OK;

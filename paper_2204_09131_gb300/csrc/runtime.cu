@@ -116,12 +116,14 @@ isycos_status check_window(isycos_ctx *ctx, const isycos_window &w, int k) {
     return ISYCOS_OK;
 }
 
-// Smallest window that takes the sorted (sub-quadratic) path: ISYCOS_OPT_KERNEL 1 keeps
-// everything on the brute-force path; 0 (auto) and 2 send the windows that run one per CTA
-// (more than 1024 points with 1024 threads per CTA) up to kSortMax to the sorted path.
-int sort_threshold(const isycos_ctx *ctx) {
-    if (ctx->opt_kernel == 1) return INT32_MAX;
-    return 1025;
+// Buckets that take the sorted (sub-quadratic) path: ISYCOS_OPT_KERNEL 1 keeps everything on
+// the brute-force path, 2 sends every eligible window (257..kSortMax points, one per CTA) to
+// the sorted path, 0 (auto) uses the buckets isycos_autotune chose for k, else 1025..4096.
+uint32_t sort_mask(const isycos_ctx *ctx, int k) {
+    if (ctx->opt_kernel == 1) return 0;
+    if (ctx->opt_kernel == 2) return kSortBuckets;
+    if (k >= 1 && k <= kMaxK && ctx->tuned[k]) return ctx->tuned_sort_mask[k];
+    return kDefaultSortBuckets;
 }
 
 // Build the persistent launch's bucket table for items already sorted by slot.
@@ -166,14 +168,15 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     if (n <= 0) return ISYCOS_OK;
     if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
     int max_m = 0, max_sorted = 0;
-    const int sort_min = sort_threshold(ctx);
+    const uint32_t smask = sort_mask(ctx, k);
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
     std::vector<int32_t> &slot = L.h_slot;
     slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         max_m = std::max(max_m, w[i].m);
-        if (w[i].m >= sort_min && w[i].m <= kSortMax) max_sorted = std::max(max_sorted, w[i].m);
+        if (w[i].m <= kSortMax && ((smask >> size_bucket(w[i].m)) & 1u))
+            max_sorted = std::max(max_sorted, w[i].m);
         pairs += (int64_t)w[i].m * (w[i].m - 1);
         slot[i] = bucket_slot(w[i].m);
         count[slot[i]]++;
@@ -237,7 +240,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     a.c = nx ? reinterpret_cast<int32_t *>(L.d_c.p) : nullptr;
     a.k = k;
     a.nt = nt;
-    a.sort_min = sort_min;
+    a.sort_mask = smask;
     a.est = est;
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
@@ -646,8 +649,11 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     cudaStream_t st = pick_stream(ctx, cuda_stream);
     isycos_status rc;
     if ((rc = sync_series_table(ctx, st))) return rc;
-    const int sort_min = sort_threshold(ctx);
-    const int max_sorted = max_m >= sort_min ? std::min(max_m, kSortMax) : 0;
+    const uint32_t smask = sort_mask(ctx, k);
+    // windows are sized on the device: room for the largest window a set bucket allows
+    int max_sorted = 0;
+    for (int b = 1; b < 31; ++b)
+        if (((smask >> b) & 1u) && (1 << (b - 1)) < max_m) max_sorted = std::min(std::min(max_m, 1 << b), kSortMax);
     const int nt = batched_threads(max_m, max_sorted);
     const size_t smem = batched_smem(max_m, nt, max_sorted);
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
@@ -691,7 +697,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.nx = a.ny = a.c = nullptr;
     a.k = k;
     a.nt = nt;
-    a.sort_min = sort_min;
+    a.sort_mask = smask;
     a.est = ctx->opt_estimator;
     e = launch_batched(a, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
@@ -825,6 +831,10 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) 
         case ISYCOS_OPT_ESTIMATOR:
             if (value < 0 || value > 1) break;
             ctx->opt_estimator = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_SPECULATION:
+            if (value < 0 || value > 16) break;
+            ctx->opt_spec_climbs = (int)value;
             return ISYCOS_OK;
         default:
             return fail(ctx, ISYCOS_E_INVAL, "unknown option %d", option);

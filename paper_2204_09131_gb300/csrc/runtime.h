@@ -102,6 +102,10 @@ struct isycos_ctx {
     int opt_kernel = 0;
     int opt_incremental = 1;
     int opt_estimator = 0;   // estimator of the direct window-MI entry points
+    int opt_spec_climbs = 3; // SYCOS_BU climbs speculated ahead
+    // sorted-path buckets chosen by isycos_autotune, per k (0: not tuned, use the default)
+    uint32_t tuned_sort_mask[ISYCOS_MAX_K + 1] = {0};
+    bool tuned[ISYCOS_MAX_K + 1] = {false};
     int serve_slots = 64;
     int serve_queue = 100000;
 
@@ -148,8 +152,8 @@ void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches
 
 cudaStream_t pick_stream(isycos_ctx *ctx, void *s);
 
-// Smallest window size of the sorted (sub-quadratic) MI path for this context.
-int sort_threshold(const isycos_ctx *ctx);
+// Size buckets whose windows take the sorted (sub-quadratic) MI path for k neighbours.
+uint32_t sort_mask(const isycos_ctx *ctx, int k);
 
 // A window sequence of one pair for the incremental kernel: result i goes to out[out_idx[i]]
 // (out_idx < 0: evaluated for its state only, result dropped).

@@ -59,6 +59,7 @@ isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchPar
     o->estimator = in->estimator;
     if (o->estimator != 0 && o->estimator != 1)
         return fail(ctx, ISYCOS_E_INVAL, "estimator must be 0 or 1");
+    o->spec_climbs = ctx->opt_spec_climbs;
     return ISYCOS_OK;
 }
 
@@ -540,15 +541,14 @@ private:
     // Speculation across climbs.  Most climbs end where they stand; the next climb then starts
     // at max(t_e + 1, c + s_min) with a window of s_min points and first asks its start
     // window and rings.  When a round goes to the GPU anyway, also ask those windows for the
-    // next kSpecClimbs climbs, assuming each ends at its start.  Their scores are cached and
-    // read only if a climb does start there; the decisions are unchanged.
-    static constexpr int kSpecClimbs = 3;
+    // next prm.spec_climbs climbs, assuming each ends at its start.  Their scores are cached
+    // and read only if a climb does start there; the decisions are unchanged.
     void speculate_next_climbs() {
         if (prm.t_max_idle < 0 || prm.max_steps <= 0) return;
         const int64_t d = prm.delta_bu, sm = prm.s_min;
         const int depth = std::min(prm.t_max_idle + 1, spec_depth_for(sm));
         int64_t c = std::max(we_ + 1, c_ + sm);
-        for (int j = 0; j < kSpecClimbs; ++j, c += sm) {
+        for (int j = 0; j < prm.spec_climbs; ++j, c += sm) {
             if (c + sm > t_end) return;
             const int64_t cs = c, ce = c + sm - 1;
             if (!grid_.on_lattice(cs, ce, d)) return;   // cached only on the grid's lattice

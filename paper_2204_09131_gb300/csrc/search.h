@@ -27,6 +27,7 @@ struct SearchParams {
     double sel_alpha, sel_rho;
     int chunks;                        // Algorithm 4 (<= 1: unchunked)
     int estimator;                     // 0: KSG estimator 2, 1: KSG estimator 1
+    int spec_climbs;                   // SYCOS_BU climbs speculated ahead (context option)
 };
 
 isycos_status resolve_params(isycos_ctx *ctx, const isycos_params *in, SearchParams *out);

@@ -246,16 +246,26 @@ def test_sorted_path_equals_brute_force(ctx):
              (np.full(n, 2.5, np.float32), base), (np.round(base).astype(np.float32), -base)]
     sizes = [1025, 1500, 2048, 3001, 4096]
     starts = [11, 3000, 7000, 12000, 15000]
+    # windows of at most 1024 points run the sorted path in 256-thread CTAs
+    small_sizes = [257, 300, 513, 700, 1000, 1024, 64, 100]
+    small_starts = [5, 2000, 4000, 6000, 9000, 12000, 15000, 17000]
     for ci, (xx, yy) in enumerate(cases):
         xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
+        for st_, sz_ in ((starts, sizes), (small_starts, small_sizes)):
+            w = api.windows_array(xs, ys, st_, sz_)
+            res2 = {}
+            for opt in (1, 2):
+                api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+                res2[opt] = api.isycos_mi_windows_points(ctx, w, 4)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+            for a, b in zip(res2[1], res2[2]):
+                assert np.array_equal(a, b), (ci, sz_)
         w = api.windows_array(xs, ys, starts, sizes)
         res = {}
         for opt in (1, 2):
             api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
             res[opt] = api.isycos_mi_windows_points(ctx, w, 4)
         api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
-        for a, b in zip(res[1], res[2]):
-            assert np.array_equal(a, b), ci
         if ci < 3:
             r = O.ksg_window(xx[3000:4500], yy[3000:4500], 4, points=False)
             assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
@@ -346,3 +356,28 @@ def test_estimator1_sorted_plain_and_device_paths(ctx):
         assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
         api.isycos_drop_series(ctx, xs)
         api.isycos_drop_series(ctx, ys)
+
+
+def test_autotune_changes_speed_not_results(ctx):
+    """isycos_autotune times the brute-force and sorted paths per eligible bucket and keeps
+    the faster; every result is the same before and after, and the counters are untouched."""
+    api = _api()
+    n = 20000
+    x, y, _ = synth.planted_pair(8, 5, n)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    sizes = [100, 700, 1025, 1536, 2048, 2049, 3072, 4096, 5000]
+    starts = [(997 * i) % (n - 5000) for i in range(len(sizes))]
+    w = api.windows_array(xs, ys, starts, sizes)
+    before = api.isycos_mi_windows(ctx, w, 4)
+    st0 = api.isycos_get_stats(ctx)
+    tune = api.isycos_autotune(ctx, 4)
+    st1 = api.isycos_get_stats(ctx)
+    assert st1["windows"] == st0["windows"] and st1["launches"] == st0["launches"]
+    assert set(tune["window_size"]) == {9, 10, 11, 12} and set(tune["sorted_buckets"]) <= {9, 10, 11, 12}
+    assert all(v > 0 for v in tune["brute_ms"].values()) and all(v > 0 for v in tune["sorted_ms"].values())
+    for b in (9, 10, 11, 12):
+        assert (b in tune["sorted_buckets"]) == (tune["sorted_ms"][b] < tune["brute_ms"][b])
+    after = api.isycos_mi_windows(ctx, w, 4)
+    assert np.array_equal(before, after)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)

@@ -362,3 +362,30 @@ def test_search_with_estimator1_matches_oracle(ctx, extra):
     assert st["decided_windows"] == n
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def test_speculation_depth_changes_work_not_results(ctx):
+    """ISYCOS_OPT_SPECULATION sets how many later BU climbs are asked ahead; the windows and
+    the decided-window count stay those of the oracle for every depth."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, pruning=1, seed=31, mode=1)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    okw = dict(kw)
+    okw.pop("mode")
+    ref, n = O.search_bu(x, y, **okw)
+    launches = {}
+    try:
+        for depth in (0, 1, 3, 8):
+            api.isycos_set_option(ctx, api.OPT_SPECULATION, depth)
+            api.isycos_reset_stats(ctx)
+            got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+            st = api.isycos_get_stats(ctx)
+            _same(got, ref)
+            assert st["decided_windows"] == n
+            launches[depth] = st["launches"]
+    finally:
+        api.isycos_set_option(ctx, api.OPT_SPECULATION, 3)
+    assert launches[3] < launches[0]
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
