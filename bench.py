@@ -497,10 +497,13 @@ def main():
         t0 = time.perf_counter()
         rb = api.isycos_mi_windows(ctx, wr, PARAMS["k"])
         t_batch = time.perf_counter() - t0
+        diff = np.nonzero(rp["s_psi"] != rb["s_psi"])[0]
         plain = {"windows": int(len(wr)), "plain_evals_per_s": round(len(wr) / t_plain, 1),
                  "batched_evals_per_s": round(len(wr) / t_batch, 1),
                  "speedup": round(t_plain / t_batch, 1),
-                 "same_results": bool(np.array_equal(rp["s_psi"], rb["s_psi"]))}
+                 "same_results": bool(diff.size == 0)}
+        if diff.size:
+            plain["differing"] = {"count": int(diff.size), "sizes": [int(v) for v in wr["m"][diff[:8]]]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

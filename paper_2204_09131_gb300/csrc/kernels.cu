@@ -260,8 +260,9 @@ __device__ __forceinline__ uint32_t fkey(float f) {
 template <int NT, typename T>
 __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all threads
     // Element i is handled by thread i mod NT, so a step with partner distance j < 32 pairs
-    // elements of the same warp: it needs only a warp barrier before the next step, unless
-    // that next step reaches across warps.
+    // elements of the same warp.  Between two steps that both stay inside warps a warp
+    // barrier suffices; when either step reaches across warps (j >= 32), the whole CTA must
+    // wait.
     for (int k2 = 2; k2 <= N; k2 <<= 1)
         for (int j = k2 >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < N; i += NT) {
@@ -276,7 +277,7 @@ __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all
                 }
             }
             const int jn = j > 1 ? (j >> 1) : ((k2 << 1) <= N ? k2 : 0);   // the next step's j
-            if (jn >= 32 || jn == 0) __syncthreads();
+            if (j >= 32 || jn >= 32 || jn == 0) __syncthreads();
             else __syncwarp();
         }
 }

@@ -325,9 +325,11 @@ public:
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
         rings_.resize((size_t)prm.t_max_idle + 2);
-        // a round reaches at most T_maxIdle + 1 cells around the window, and the speculative
-        // climbs some s_min / delta cells beyond it
-        grid_.init(4 * (prm.t_max_idle + 2) + 8 * std::max<int64_t>(1, prm.s_min / std::max(1, prm.delta_bu)));
+        // the cells one round asks span T_maxIdle + 1 cells around the window and the windows
+        // of the climbs asked ahead, s_min / delta cells apart: the direct-mapped array must
+        // be wider than that span so that they do not evict one another
+        const int64_t step = std::max<int64_t>(1, prm.s_min / std::max(1, prm.delta_bu));
+        grid_.init((int)((prm.spec_climbs + 1) * step + 2 * (prm.t_max_idle + 2) + 4));
     }
 
 private:

@@ -381,3 +381,64 @@ def test_autotune_changes_speed_not_results(ctx):
     assert np.array_equal(before, after)
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def test_ring_shaped_batch_all_paths_agree(ctx):
+    """2,000 windows of 32..1024 points (log-uniform, the shape of BU rings): the plain
+    one-window-per-launch form, the brute-force batch and the sorted-path batch give the same
+    integers, and sampled windows equal the oracle."""
+    api = _api()
+    n = 100000
+    x, y, _ = synth.planted_pair(2, 0, n)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    rng = np.random.default_rng(5)
+    sizes = np.exp(rng.uniform(np.log(32), np.log(1024), 2000)).astype(int)
+    starts = np.array([int(rng.integers(0, n - m)) for m in sizes])
+    w = api.windows_array(xs, ys, starts, sizes)
+    res = {}
+    try:
+        for opt in (1, 2):
+            api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+            res[opt] = api.isycos_mi_windows(ctx, w, 4)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+    plain = api.isycos_mi_windows_plain(ctx, w, 4)
+    bad = np.nonzero(res[1]["s_psi"] != res[2]["s_psi"])[0]
+    assert bad.size == 0, ("sorted vs brute", bad[:10], sizes[bad[:10]])
+    bad = np.nonzero(plain["s_psi"] != res[1]["s_psi"])[0]
+    assert bad.size == 0, ("plain vs brute", bad[:10], sizes[bad[:10]])
+    for i in range(0, 2000, 97):
+        s, m = int(starts[i]), int(sizes[i])
+        r = O.ksg_window(x[s:s + m], y[s:s + m], 4, points=False)
+        assert res[1]["s_psi"][i] == r["s_psi"] and res[1]["mi"][i] == r["mi"], (i, m)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+
+
+def test_sorted_path_repeats_bit_exact(ctx):
+    """The sorted path's sorts and scans synchronise warps and CTAs in many small steps; a
+    missing barrier shows up as run-to-run differences.  Repeat mixed batches (256- and
+    1024-thread CTAs) and require every repeat to equal the brute-force path."""
+    api = _api()
+    n = 60000
+    x, y, _ = synth.planted_pair(2, 7, n)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    rng = np.random.default_rng(11)
+    lists = []
+    for lo, hi in ((257, 1024), (1025, 4096)):
+        sizes = rng.integers(lo, hi + 1, 600)
+        starts = np.array([int(rng.integers(0, n - m)) for m in sizes])
+        lists.append(api.windows_array(xs, ys, starts, sizes))
+    try:
+        for w in lists:
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 1)
+            ref = api.isycos_mi_windows(ctx, w, 4)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 2)
+            for rep in range(12):
+                got = api.isycos_mi_windows(ctx, w, 4)
+                bad = np.nonzero(got["s_psi"] != ref["s_psi"])[0]
+                assert bad.size == 0, (rep, bad[:8], w["m"][bad[:8]])
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
