@@ -71,7 +71,7 @@ extern "C" isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuni
         const uint32_t saved_mask = ctx->tuned_sort_mask[k];
         ctx->opt_kernel = 0;
         ctx->tuned[k] = true;
-        Lane &L = *ctx->lanes[0];
+        Lane &L = *ctx->lanes[0].load();
         const int n_w = 8 * std::max(1, ctx->n_sm);   // several waves, as in a TD layer
         res.n_windows = n_w;
         uint32_t chosen = 0;

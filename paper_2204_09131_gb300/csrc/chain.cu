@@ -428,5 +428,5 @@ extern "C" isycos_status isycos_mi_chain(isycos_ctx *ctx, int32_t xs, int32_t ys
         sp.sizes.push_back(sizes[i]);
         sp.out_idx.push_back(i);
     }
-    return engine_eval_chains(ctx, *ctx->lanes[0], &sp, 1, k, out, n_steps, pick_stream(ctx, cuda_stream));
+    return engine_eval_chains(ctx, *ctx->lanes[0].load(), &sp, 1, k, out, n_steps, pick_stream(ctx, cuda_stream));
 }

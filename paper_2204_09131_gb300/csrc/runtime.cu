@@ -143,7 +143,7 @@ static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
 }
 
 static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, int jobs_hint,
-                                 int *grid) {
+                                 int share, int *grid) {
     int per_sm = 0;
     const uint64_t key = ((uint64_t)k << 48) | ((uint64_t)nt << 32) | (uint64_t)smem;
     std::lock_guard<std::mutex> g(ctx->launch_mu);
@@ -157,6 +157,7 @@ static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, in
     }
     if (per_sm < 1) return fail(ctx, ISYCOS_E_INVAL, "kernel does not fit on an SM (smem %zu)", smem);
     int gsz = ctx->n_sm * per_sm;
+    if (share > 0 && share < 4) gsz = std::max(1, gsz * share / 4);
     if (jobs_hint > 0 && jobs_hint < gsz) gsz = jobs_hint;
     *grid = std::max(gsz, 1);
     return ISYCOS_OK;
@@ -226,7 +227,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     L.queue_clean = true;
 
     int grid;
-    if ((rc = launch_grid(ctx, k, nt, smem, batched_grid_need(T, nt), &grid))) return rc;
+    if ((rc = launch_grid(ctx, k, nt, smem, batched_grid_need(T, nt), L.slot_share, &grid))) return rc;
     BatchArgs a;
     a.items = reinterpret_cast<const WorkItem *>(reinterpret_cast<unsigned char *>(L.d_items.p) + tab_bytes);
     a.table = reinterpret_cast<const BucketTable *>(L.d_items.p);
@@ -309,24 +310,40 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
 }
 
 isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out) {
-    while ((int)ctx->lanes.size() <= i) {
-        Lane *L = new Lane();
-        cudaError_t e = cudaSuccess;
-        if (ctx->lanes.empty()) {
-            L->stream = ctx->stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
-            L->own_stream = true;
-        }
-        if (e == cudaSuccess) e = cudaEventCreate(&L->ev_start);
-        if (e == cudaSuccess) e = cudaEventCreate(&L->ev_stop);
-        if (e != cudaSuccess) {
-            delete L;
-            return cuda_fail(ctx, e, "lane creation");
-        }
-        ctx->lanes.push_back(L);
+    if (i < 0 || i >= kLaneSlots) return fail(ctx, ISYCOS_E_INVAL, "lane %d out of range", i);
+    Lane *have = ctx->lanes[i].load(std::memory_order_acquire);
+    if (have) {
+        *out = have;
+        return ISYCOS_OK;
     }
-    *out = ctx->lanes[i];
+    std::lock_guard<std::mutex> g(ctx->lane_mu);
+    if ((have = ctx->lanes[i].load(std::memory_order_acquire))) {
+        *out = have;
+        return ISYCOS_OK;
+    }
+    Lane *L = new Lane();
+    cudaError_t e = cudaSuccess;
+    if (i == 0) {
+        L->stream = ctx->stream;
+    } else {
+        // latency-bound searches get the highest stream priority, so that their small
+        // launches take CTA slots ahead of the waiting CTAs of large launches
+        int least = 0, greatest = 0;
+        if (i >= kPrioLaneBase) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking,
+                                             i >= kPrioLaneBase ? greatest : least);
+        L->own_stream = true;
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&L->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&L->ev_stop);
+    if (e != cudaSuccess) {
+        if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+        delete L;
+        return cuda_fail(ctx, e, "lane creation");
+    }
+    ctx->lanes[i].store(L, std::memory_order_release);
+    *out = L;
     return ISYCOS_OK;
 }
 
@@ -484,11 +501,12 @@ isycos_status isycos_destroy(isycos_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (float *p : ctx->series_ptr)
         if (p) cudaFree(p);
-    for (Lane *L : ctx->lanes) {
+    for (int i = 0; i < kLaneSlots; ++i) {
+        Lane *L = ctx->lanes[i].exchange(nullptr);
+        if (!L) continue;
         cudaStreamSynchronize(L->stream);
         free_lane(ctx, L);
     }
-    ctx->lanes.clear();
     DevBuf *bufs[] = {&ctx->d_series_ptr, &ctx->d_series_len, &ctx->d_table, &ctx->d_slot,
                       &ctx->d_pos, &ctx->d_bcount, &ctx->d_status, &ctx->d_plain_acc,
                       &ctx->d_dev_items, &ctx->d_dev_queue, &ctx->d_dev_table};
@@ -615,7 +633,7 @@ isycos_status isycos_mi_windows(isycos_ctx *ctx, const isycos_window *windows, i
     std::vector<HostWindow> hw;
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
-    return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
+    return engine_eval(ctx, *ctx->lanes[0].load(), hw.data(), n_w, k, out, nullptr, nullptr, nullptr,
                        pick_stream(ctx, cuda_stream), ctx->opt_estimator);
 }
 
@@ -630,7 +648,7 @@ isycos_status isycos_mi_windows_points(isycos_ctx *ctx, const isycos_window *win
     std::vector<HostWindow> hw;
     isycos_status rc = host_windows(ctx, windows, n_w, k, hw);
     if (rc) return rc;
-    return engine_eval(ctx, *ctx->lanes[0], hw.data(), n_w, k, out, nx, ny, c,
+    return engine_eval(ctx, *ctx->lanes[0].load(), hw.data(), n_w, k, out, nx, ny, c,
                        pick_stream(ctx, cuda_stream), ctx->opt_estimator);
 }
 
@@ -686,7 +704,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     if (e == cudaSuccess) e = launch_prep(pa, st, &launches);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "window preparation");
     int grid;
-    if ((rc = launch_grid(ctx, k, nt, smem, 0, &grid))) return rc;
+    if ((rc = launch_grid(ctx, k, nt, smem, 0, 4, &grid))) return rc;
     BatchArgs a;
     a.items = pa.items;
     a.table = pa.table;
@@ -734,7 +752,7 @@ isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *wind
     if (rc) return rc;
     if (n_w == 0) return ISYCOS_OK;
     cudaStream_t st = pick_stream(ctx, cuda_stream);
-    if ((rc = dev_reserve(ctx, ctx->lanes[0]->d_out, sizeof(isycos_mi_out) * n_w))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->lanes[0].load()->d_out, sizeof(isycos_mi_out) * n_w))) return rc;
     if (!ctx->d_plain_acc.p) {
         if ((rc = dev_reserve(ctx, ctx->d_plain_acc, 256))) return rc;
         cudaError_t e = cudaMemset(ctx->d_plain_acc.p, 0, 256);
@@ -742,7 +760,7 @@ isycos_status isycos_mi_windows_plain(isycos_ctx *ctx, const isycos_window *wind
     }
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(ctx->d_plain_acc.p);
     int32_t *done = reinterpret_cast<int32_t *>(acc + 2);
-    isycos_mi_out *d_out = reinterpret_cast<isycos_mi_out *>(ctx->lanes[0]->d_out.p);
+    isycos_mi_out *d_out = reinterpret_cast<isycos_mi_out *>(ctx->lanes[0].load()->d_out.p);
     int launches = 0;
     int64_t pairs = 0;
     for (int64_t i = 0; i < n_w; ++i) {

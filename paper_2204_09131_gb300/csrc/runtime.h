@@ -17,6 +17,14 @@
 
 namespace isy {
 
+// Lane indices: searches use 0 .. kMaxLanes - 1 (default priority) and kPrioLaneBase + i
+// (highest stream priority, for latency-bound searches); serving workers kServeLaneBase + w.
+constexpr int kMaxLanes = 16;
+constexpr int kServeLaneBase = 32;
+constexpr int kPrioLaneBase = 48;
+constexpr int kLaneSlots = 64;
+
+
 class Server;
 
 // A growable device buffer whose bytes count against the context's budget.
@@ -41,6 +49,8 @@ struct Lane {
     DevBuf d_chain_desc, d_chain_steps, d_chain_state, d_chain_recomp, d_chain_out;
     HostBuf h_items, h_table;          // pinned staging: table + items; results
     bool queue_clean = false;          // d_queue holds zeroed work counters
+    int slot_share = 4;                // quarters of the GPU's resident-CTA slots a launch
+                                       // of this lane may take (4: all)
     // the open launch of engine_launch
     struct Open {
         bool open = false;
@@ -85,7 +95,10 @@ struct isycos_ctx {
     // Engine state (guarded by engine_mu; lanes other than 0 are driven by helper threads
     // while the calling thread holds engine_mu).
     std::mutex engine_mu;
-    std::vector<isy::Lane *> lanes;      // lane 0 uses `stream`
+    // engine lanes by index (created on first use by get_lane under lane_mu, never moved;
+    // lane 0 uses `stream`)
+    std::atomic<isy::Lane *> lanes[isy::kLaneSlots] = {};
+    std::mutex lane_mu;
     int max_lanes = 8;
     isy::DevBuf d_table, d_slot, d_pos, d_bcount, d_status, d_plain_acc;
     isy::DevBuf d_dev_items, d_dev_queue, d_dev_table;   // asynchronous device-array path
@@ -137,9 +150,6 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
 isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                             int est, int32_t *nx, int32_t *ny, int32_t *c, cudaStream_t st);
 isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out);
-
-// Lane indices: searches use 0 .. kMaxLanes - 1, serving workers kServeLaneBase + worker.
-constexpr int kMaxLanes = 16;
 
 // Lane i of the context (created on first use; lane 0 runs on ctx->stream).
 isycos_status get_lane(isycos_ctx *ctx, int i, Lane **out);

@@ -1189,11 +1189,28 @@ static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     // its machines' rounds on its own stream, so that the sequential decision logic of many
     // queries proceeds in parallel and their batches overlap on the GPU.
     const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 3) / 4));
+    // SYCOS_TD queries make few, large launches (throughput-bound); the others many small
+    // ones (latency-bound).  When both are present they get separate lanes: the TD lanes'
+    // launches leave a quarter of the GPU's CTA slots free and the others run on
+    // high-priority streams, so that their rounds overlap the large launches instead of
+    // waiting behind them.
+    std::vector<SearchMachine *> thr, lat;
+    for (SearchMachine *m : ms) (m->prm.mode == 0 ? thr : lat).push_back(m);
+    const bool split = !thr.empty() && !lat.empty() && n_lanes >= 2;
+    const int n_thr = split ? std::max(1, n_lanes / 4) : 0;
     std::vector<Lane *> lanes((size_t)n_lanes);
-    for (int i = 0; i < n_lanes; ++i)
-        if ((rc = get_lane(ctx, i, &lanes[i]))) return rc;
     std::vector<std::vector<SearchMachine *>> parts((size_t)n_lanes);
-    for (size_t q = 0; q < ms.size(); ++q) parts[q % n_lanes].push_back(ms[q]);
+    for (int i = 0; i < n_lanes; ++i) {
+        const bool prio = split && i >= n_thr;
+        if ((rc = get_lane(ctx, prio ? kPrioLaneBase + (i - n_thr) : i, &lanes[i]))) return rc;
+        lanes[i]->slot_share = split && !prio ? 3 : 4;
+    }
+    if (split) {
+        for (size_t q = 0; q < thr.size(); ++q) parts[q % n_thr].push_back(thr[q]);
+        for (size_t q = 0; q < lat.size(); ++q) parts[n_thr + q % (n_lanes - n_thr)].push_back(lat[q]);
+    } else {
+        for (size_t q = 0; q < ms.size(); ++q) parts[q % n_lanes].push_back(ms[q]);
+    }
     std::vector<isycos_status> st((size_t)n_lanes, ISYCOS_OK);
     std::vector<std::thread> th;
     const int dev = ctx->device;

@@ -51,7 +51,6 @@ public:
         for (auto &t : th_) t.join();
     }
 
-    static constexpr int kServeLaneBase = 32;
 
     isycos_status submit(int32_t xs, int32_t ys, int64_t tb, int64_t te, const SearchParams &p,
                          uint64_t *ticket) {
