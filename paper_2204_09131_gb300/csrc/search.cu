@@ -1193,28 +1193,34 @@ static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     // ones (latency-bound).  When both are present they get separate lanes: the TD lanes'
     // launches leave a quarter of the GPU's CTA slots free and the others run on
     // high-priority streams, so that their rounds overlap the large launches instead of
-    // waiting behind them.
+    // waiting behind them.  The TD lanes, which mostly wait on their launches, come in
+    // addition to the lanes of the latency-bound queries.
     std::vector<SearchMachine *> thr, lat;
     for (SearchMachine *m : ms) (m->prm.mode == 0 ? thr : lat).push_back(m);
-    const bool split = !thr.empty() && !lat.empty() && n_lanes >= 2;
-    const int n_thr = split ? std::max(1, n_lanes / 4) : 0;
-    std::vector<Lane *> lanes((size_t)n_lanes);
-    std::vector<std::vector<SearchMachine *>> parts((size_t)n_lanes);
-    for (int i = 0; i < n_lanes; ++i) {
+    const bool split = !thr.empty() && !lat.empty();
+    int n_thr = 0, n_all = n_lanes;
+    if (split) {
+        const int n_lat = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, ((int64_t)lat.size() + 3) / 4));
+        n_thr = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, ctx->max_lanes / 4), ((int64_t)thr.size() + 3) / 4));
+        n_all = n_thr + n_lat;
+    }
+    std::vector<Lane *> lanes((size_t)n_all);
+    std::vector<std::vector<SearchMachine *>> parts((size_t)n_all);
+    for (int i = 0; i < n_all; ++i) {
         const bool prio = split && i >= n_thr;
         if ((rc = get_lane(ctx, prio ? kPrioLaneBase + (i - n_thr) : i, &lanes[i]))) return rc;
         lanes[i]->slot_share = split && !prio ? 3 : 4;
     }
     if (split) {
         for (size_t q = 0; q < thr.size(); ++q) parts[q % n_thr].push_back(thr[q]);
-        for (size_t q = 0; q < lat.size(); ++q) parts[n_thr + q % (n_lanes - n_thr)].push_back(lat[q]);
+        for (size_t q = 0; q < lat.size(); ++q) parts[n_thr + q % (n_all - n_thr)].push_back(lat[q]);
     } else {
         for (size_t q = 0; q < ms.size(); ++q) parts[q % n_lanes].push_back(ms[q]);
     }
-    std::vector<isycos_status> st((size_t)n_lanes, ISYCOS_OK);
+    std::vector<isycos_status> st((size_t)n_all, ISYCOS_OK);
     std::vector<std::thread> th;
     const int dev = ctx->device;
-    for (int i = 1; i < n_lanes; ++i)
+    for (int i = 1; i < n_all; ++i)
         th.emplace_back([&, i] {
             cudaSetDevice(dev);
             st[i] = run_machines(ctx, *lanes[i], parts[i], lanes[i]->stream);
