@@ -215,13 +215,13 @@ def reference_arm(args):
         return
     pairs = make_pairs(0, 1, args.length)
     vals = []
-    for _ in range(args.warmup):
-        pass
+    t0 = time.perf_counter()
     for _ in range(args.steps):
         vals.append(cpu_baseline(pairs))
+    ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     v = statistics.median([c["value"] for c in vals])
     line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "isycos-td-bu-64x100k", "pairs": 1, "length": 12000,
