@@ -57,6 +57,8 @@ struct BatchArgs {
     uint32_t sort_mask;          // bit b set: windows of bucket b (2^(b-1) < m <= 2^b) that
                                  // run one per CTA take the sorted path
     int32_t est;                 // 0: Kraskov's second estimator (Eq. KSGmi), 1: the first
+    int32_t pad;
+    double inv_k;                // 1 / k correctly rounded (estimator 0), or 0 (estimator 1)
 };
 
 // Device-side preparation of a window list held in device memory.

@@ -63,14 +63,16 @@ __device__ __forceinline__ void list_insert(float (&bd)[K1], int (&bj)[K1], floa
 }
 
 // Canonical binary64 evaluation of the window scalars from the exact integer sums.
+// inv_k = 1/k (correctly rounded, as computed on the host), or 0 for Kraskov's first
+// estimator, which has no -1/k term (psi_k - 0 is psi_k exactly).  The binary64 work here
+// runs on a narrow pipe: callers batch windows so that the lanes of one warp finish
+// different windows together.
 __device__ __forceinline__ void write_result(isycos_mi_out *o, int k, int m, long long s_psi,
                                              long long s_log, const long long *psi_fx,
-                                             const long long *log_fx, int est) {
+                                             const long long *log_fx, double inv_k) {
     const double two_m32 = 2.3283064365386962890625e-10;  // 2^-32
     const double psi_k = __dmul_rn(__ll2double_rn(psi_fx[k]), two_m32);
     const double psi_m = __dmul_rn(__ll2double_rn(psi_fx[m]), two_m32);
-    // Kraskov's first estimator has no -1/k term (psi_k - 0 is psi_k exactly)
-    const double inv_k = est ? 0.0 : __ddiv_rn(1.0, (double)k);
     const double mean_psi = __ddiv_rn(__dmul_rn(__ll2double_rn(s_psi), two_m32), (double)m);
     const double mi = __dsub_rn(__dadd_rn(__dsub_rn(psi_k, inv_k), psi_m), mean_psi);
     const double ln_m = __dmul_rn(__ll2double_rn(log_fx[m]), two_m32);
@@ -479,6 +481,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
     extern __shared__ float2 tile[];
     constexpr int W = NT / 32;
     __shared__ long long acc_psi[W], acc_log[W];
+    __shared__ int fin_out[W], fin_m[W];   // the job's items, finished by the lanes of warp 0
     __shared__ int job_s;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const BucketTable *T = a.table;
@@ -504,6 +507,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         if (lane == 0 && sub == 0) {
             acc_psi[slot] = 0;
             acc_log[slot] = 0;
+            fin_out[slot] = has ? it.out : -1;
+            fin_m[slot] = it.m;
         }
         __syncthreads();
         if (has) {
@@ -530,12 +535,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
             }
         }
         __syncthreads();
-        if (has && sub == 0 && lane == 0)
-            write_result(a.out + it.out, a.k, it.m, acc_psi[slot], acc_log[slot], a.psi_fx, a.log_fx, a.est);
+        if (warp == 0 && lane < per_job && fin_out[lane] >= 0)
+            write_result(a.out + fin_out[lane], a.k, fin_m[lane], acc_psi[lane], acc_log[lane],
+                         a.psi_fx, a.log_fx, a.inv_k);
     }
     // Small windows (m <= 64): one warp each, staged in the warp's own slice, no CTA barrier.
     float2 *ws = tile + warp * kBlockPts;
     const int first = T->small_first, last = T->n_items;
+    // lane r keeps the sums of the r-th pending window of this warp; the lanes finish up to
+    // 32 windows together
+    long long pend_psi = 0, pend_log = 0;
+    int pend_m = 0, pend_out = 0, n_pend = 0;
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(a.queue + 1, 1);
@@ -558,8 +568,19 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
             ksg_block<K1, 2>(ws, it.m, 0, lane, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
         lp = warp_sum64(lp);
         ll = warp_sum64(ll);
-        if (lane == 0) write_result(a.out + it.out, a.k, it.m, lp, ll, a.psi_fx, a.log_fx, a.est);
+        if (lane == n_pend) {
+            pend_psi = lp;
+            pend_log = ll;
+            pend_m = it.m;
+            pend_out = it.out;
+        }
+        if (++n_pend == 32) {
+            write_result(a.out + pend_out, a.k, pend_m, pend_psi, pend_log, a.psi_fx, a.log_fx, a.inv_k);
+            n_pend = 0;
+        }
     }
+    if (lane < n_pend)
+        write_result(a.out + pend_out, a.k, pend_m, pend_psi, pend_log, a.psi_fx, a.log_fx, a.inv_k);
     // The last CTA to finish zeroes the work counters for the next launch on this buffer:
     // every other CTA has taken its last job before it counts itself out.
     __syncthreads();
@@ -616,7 +637,7 @@ __global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const
         __threadfence();
         const long long tp = (long long)atomicAdd(acc, 0ull);
         const long long tl = (long long)atomicAdd(acc + 1, 0ull);
-        write_result(out, k, it.m, tp, tl, psi_fx, log_fx, est);
+        write_result(out, k, it.m, tp, tl, psi_fx, log_fx, est ? 0.0 : __ddiv_rn(1.0, (double)k));
         acc[0] = 0;
         acc[1] = 0;
         *done = 0;

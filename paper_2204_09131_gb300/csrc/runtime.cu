@@ -243,6 +243,8 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     a.nt = nt;
     a.sort_mask = smask;
     a.est = est;
+    a.pad = 0;
+    a.inv_k = est ? 0.0 : 1.0 / (double)k;
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
@@ -717,6 +719,8 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.nt = nt;
     a.sort_mask = smask;
     a.est = ctx->opt_estimator;
+    a.pad = 0;
+    a.inv_k = a.est ? 0.0 : 1.0 / (double)k;
     e = launch_batched(a, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
     add_stats(ctx, n_w, 0, launches + 1, 1, 0);
