@@ -301,8 +301,9 @@ isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int
 /* Autotuner.  The paper has no counterpart: its kNN search is a CPU index (Sec. 7.1).  For
  * k neighbours, times the brute-force and the sorted-strip MI paths on a seeded probe pair
  * (x ~ N(0,1), y = 0.6 x + 0.8 N(0,1), 65,536 points, uploaded and dropped by the call)
- * with one launch of n_windows windows of the middle size of each bucket the sorted path can
- * take (windows of 257..4096 points), and keeps the faster path per bucket for this context
+ * with one launch of n_windows windows (fewer for the two largest buckets) of the middle size
+ * of each bucket the sorted path can take (windows of 257..16384 points), and keeps the faster
+ * path per bucket for this context
  * and k (used while ISYCOS_OPT_KERNEL is 0, the default).  Results are identical on both
  * paths; only speed changes.  Statistics are left as they were.  out may be NULL.
  * Errors: E_INVAL (k), E_NOMEM (budget), E_CUDA. */
@@ -311,7 +312,8 @@ typedef struct {
     uint32_t sorted_buckets;   /* bit b set: windows with 2^(b-1) < m <= 2^b take the sorted
                                   path                                                      */
     int32_t window_size[15];   /* probe window size per bucket (0: bucket not probed)       */
-    int32_t n_windows;         /* windows per probe launch (8 per SM)                        */
+    int32_t n_windows;         /* windows per probe launch (8 per SM; 2 and 1 per SM for the
+                                  buckets of 4097..8192 and 8193..16384 points)             */
     double brute_ms[15];       /* best of three launch times, brute-force path               */
     double sorted_ms[15];      /* best of three launch times, sorted-strip path              */
 } isycos_tuning;   /* 312 bytes */
@@ -319,8 +321,8 @@ isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuning *out);
 
 /* Options (isycos_set_option).  Values are documented per option. */
 #define ISYCOS_OPT_KERNEL 1        /* 0 auto (default: the buckets isycos_autotune chose, else
-                                      sorted for 1025..4096 points), 1 brute force, 2 sorted
-                                      for every window of 257..4096 points                  */
+                                      sorted for 1025..16384 points), 1 brute force, 2 sorted
+                                      for every window of 257..16384 points                 */
 #define ISYCOS_OPT_INCREMENTAL 2   /* searches: 0 off, 1 auto (default), 2 always           */
 #define ISYCOS_OPT_SERVE_SLOTS 3   /* serving: most queries admitted at once (default 64)   */
 #define ISYCOS_OPT_SERVE_QUEUE 4   /* serving: most queries waiting (default 100000)        */

@@ -72,13 +72,16 @@ extern "C" isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuni
         ctx->opt_kernel = 0;
         ctx->tuned[k] = true;
         Lane &L = *ctx->lanes[0].load();
-        const int n_w = 8 * std::max(1, ctx->n_sm);   // several waves, as in a TD layer
-        res.n_windows = n_w;
+        // several waves, as in a TD layer (fewer for the largest windows, whose brute-force
+        // launches take tens of milliseconds)
+        const int n_sm = std::max(1, ctx->n_sm);
+        res.n_windows = 8 * n_sm;
         uint32_t chosen = 0;
-        std::vector<HostWindow> w((size_t)n_w);
-        std::vector<isycos_mi_out> r((size_t)n_w);
+        std::vector<HostWindow> w((size_t)res.n_windows);
+        std::vector<isycos_mi_out> r((size_t)res.n_windows);
         for (int b = 0; b < 15 && !rc; ++b) {
             if (!((kSortBuckets >> b) & 1u)) continue;
+            const int n_w = b <= 12 ? 8 * n_sm : (b == 13 ? 2 * n_sm : n_sm);
             const int m = 3 << (b - 2);   // the middle of bucket b: 2^(b-1) < m <= 2^b
             res.window_size[b] = m;
             for (int i = 0; i < n_w; ++i)

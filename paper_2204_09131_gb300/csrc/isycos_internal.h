@@ -59,6 +59,8 @@ struct BatchArgs {
     int32_t est;                 // 0: Kraskov's second estimator (Eq. KSGmi), 1: the first
     int32_t pad;
     double inv_k;                // 1 / k correctly rounded (estimator 0), or 0 (estimator 1)
+    unsigned char *gscratch;     // sorted-path scratch of windows above kSortMax points: one
+    int64_t gscratch_stride;     // slice of gscratch_stride bytes per CTA (nullptr: none)
 };
 
 // Device-side preparation of a window list held in device memory.
@@ -133,13 +135,15 @@ inline int batched_grid_need(const BucketTable &T, int nt) {
     return T.total_jobs + (T.n_items - T.small_first + W - 1) / W;
 }
 
-// Largest window of the sorted path (its sort keys and records share the CTA's shared memory).
+// Largest window whose sorted-path scratch (sort keys, records) shares the CTA's shared
+// memory; larger windows, up to kMaxM, keep it in a slice of global memory per CTA (it stays
+// in L2).
 constexpr int kSortMax = 4096;
 // Buckets the sorted path can take: windows of 257..4096 points, which run one per CTA (a
 // 256-thread CTA up to 1024 points, a 1024-thread CTA above); the path is used for 1025..4096
 // points unless isycos_autotune chose otherwise.
-constexpr uint32_t kSortBuckets = (1u << 9) | (1u << 10) | (1u << 11) | (1u << 12);
-constexpr uint32_t kDefaultSortBuckets = (1u << 11) | (1u << 12);
+constexpr uint32_t kSortBuckets = (1u << 9) | (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14);
+constexpr uint32_t kDefaultSortBuckets = (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14);
 __host__ __device__ inline int size_bucket(int m) {   // smallest b with m <= 2^b
     int b = 0;
     while ((1 << b) < m) ++b;
@@ -150,11 +154,12 @@ __host__ __device__ inline int size_bucket(int m) {   // smallest b with m <= 2^
 // (8 bytes per slot, the slot count rounded up to a power of two), the x-ordered records
 // (16 bytes per point), per-point d_x, d_y and multiplicity (12 bytes), a work counter.
 __host__ __device__ inline size_t sorted_off(int m) { return ((size_t)m * 8 + 15) & ~(size_t)15; }
-__host__ __device__ inline size_t sorted_smem(int m) {
+__host__ __device__ inline size_t sorted_scratch(int m) {   // the part after the window
     int n = 1;
     while (n < m) n <<= 1;
-    return sorted_off(m) + (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16;
+    return (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16;
 }
+__host__ __device__ inline size_t sorted_smem(int m) { return sorted_off(m) + sorted_scratch(m); }
 
 // Shared memory of a batched launch whose largest window has max_m points; max_sorted is the
 // largest window that takes the sorted path (0: none).
@@ -167,7 +172,8 @@ inline size_t batched_smem(int max_m, int nt, int max_sorted = 0) {
 
 // Threads per CTA chosen for a batch whose largest window has max_m points and whose
 // largest sorted-path window has max_sorted points (the sorted path runs one window per CTA:
-// above 1024 points it takes 1024 threads, which hide its dependent loads).
+// above 1024 points it takes 1024 threads, which hide its dependent loads).  max_sorted
+// counts only windows whose scratch is in shared memory (at most kSortMax points).
 inline int batched_threads(int max_m, int max_sorted = 0) {
     return (max_m > 8192 || max_sorted > 1024) ? 1024 : 256;
 }

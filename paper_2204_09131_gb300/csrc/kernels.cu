@@ -519,9 +519,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                 nyo = a.ny + it.pts;
                 co = a.c + it.pts;
             }
-            if (per_job == 1 && it.m <= kSortMax && ((a.sort_mask >> (32 - __clz(it.m - 1))) & 1u)) {
-                ksg_window_sorted<K1, NT>(s, it.m, reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m),
-                                          a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
+            const bool sorted = per_job == 1 && ((a.sort_mask >> (32 - __clz(it.m - 1))) & 1u) &&
+                                (it.m <= kSortMax || a.gscratch != nullptr);
+            if (sorted) {
+                unsigned char *scr = it.m <= kSortMax
+                                         ? reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m)
+                                         : a.gscratch + (size_t)blockIdx.x * (size_t)a.gscratch_stride;
+                ksg_window_sorted<K1, NT>(s, it.m, scr, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
             } else {
                 const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
                 for (int b = sub; b < nblk; b += wpw)

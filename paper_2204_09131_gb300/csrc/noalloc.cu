@@ -228,6 +228,8 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     a.est = 0;                // Kraskov's second estimator (Eq. KSGmi)
     a.pad = 0;
     a.inv_k = 1.0 / (double)k;
+    a.gscratch = nullptr;
+    a.gscratch_stride = 0;
     if (launch_batched(a, n_sm * per_sm, smem, st) != cudaSuccess) return ISYCOS_E_CUDA;
     return ISYCOS_OK;
 }

@@ -168,7 +168,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     L.open.open = false;
     if (n <= 0) return ISYCOS_OK;
     if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
-    int max_m = 0, max_sorted = 0;
+    int max_m = 0, max_sorted = 0, max_sorted_glob = 0;
     const uint32_t smask = sort_mask(ctx, k);
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
@@ -176,14 +176,16 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         max_m = std::max(max_m, w[i].m);
-        if (w[i].m <= kSortMax && ((smask >> size_bucket(w[i].m)) & 1u))
-            max_sorted = std::max(max_sorted, w[i].m);
+        if ((smask >> size_bucket(w[i].m)) & 1u) {
+            if (w[i].m <= kSortMax) max_sorted = std::max(max_sorted, w[i].m);
+            else max_sorted_glob = std::max(max_sorted_glob, w[i].m);
+        }
         pairs += (int64_t)w[i].m * (w[i].m - 1);
         slot[i] = bucket_slot(w[i].m);
         count[slot[i]]++;
         total_pts += w[i].m;
     }
-    const int nt = batched_threads(max_m, max_sorted);
+    const int nt = batched_threads(max_m, std::max(max_sorted, max_sorted_glob));
     const size_t smem = batched_smem(max_m, nt, max_sorted);
     isycos_status rc;
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
@@ -228,6 +230,12 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
 
     int grid;
     if ((rc = launch_grid(ctx, k, nt, smem, batched_grid_need(T, nt), L.slot_share, &grid))) return rc;
+    // sorted-path scratch of the windows above kSortMax points: one slice per CTA
+    size_t g_stride = 0;
+    if (max_sorted_glob > 0) {
+        g_stride = (sorted_scratch(max_sorted_glob) + 255) & ~(size_t)255;
+        if ((rc = dev_reserve(ctx, L.d_gscratch, g_stride * (size_t)grid))) return rc;
+    }
     BatchArgs a;
     a.items = reinterpret_cast<const WorkItem *>(reinterpret_cast<unsigned char *>(L.d_items.p) + tab_bytes);
     a.table = reinterpret_cast<const BucketTable *>(L.d_items.p);
@@ -245,6 +253,8 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     a.est = est;
     a.pad = 0;
     a.inv_k = est ? 0.0 : 1.0 / (double)k;
+    a.gscratch = max_sorted_glob > 0 ? reinterpret_cast<unsigned char *>(L.d_gscratch.p) : nullptr;
+    a.gscratch_stride = (int64_t)g_stride;
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
@@ -353,14 +363,14 @@ void lane_release(isycos_ctx *ctx, Lane &L) {
     cudaStreamSynchronize(L.stream);
     DevBuf *bufs[] = {&L.d_items, &L.d_queue, &L.d_out, &L.d_nx, &L.d_ny, &L.d_c,
                       &L.d_chain_desc, &L.d_chain_steps, &L.d_chain_state,
-                      &L.d_chain_recomp, &L.d_chain_out};
+                      &L.d_chain_recomp, &L.d_chain_out, &L.d_gscratch};
     for (DevBuf *b : bufs) dev_release(ctx, *b);
 }
 
 static void free_lane(isycos_ctx *ctx, Lane *L) {
     DevBuf *bufs[] = {&L->d_items, &L->d_queue, &L->d_out, &L->d_nx, &L->d_ny, &L->d_c,
                       &L->d_chain_desc, &L->d_chain_steps, &L->d_chain_state,
-                      &L->d_chain_recomp, &L->d_chain_out};
+                      &L->d_chain_recomp, &L->d_chain_out, &L->d_gscratch};
     for (DevBuf *b : bufs) dev_release(ctx, *b);
     if (L->h_items.p) cudaFreeHost(L->h_items.p);
     if (L->h_table.p) cudaFreeHost(L->h_table.p);
@@ -721,6 +731,8 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.est = ctx->opt_estimator;
     a.pad = 0;
     a.inv_k = a.est ? 0.0 : 1.0 / (double)k;
+    a.gscratch = nullptr;   // windows above kSortMax points take the brute-force path here
+    a.gscratch_stride = 0;
     e = launch_batched(a, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "MI kernel launch");
     add_stats(ctx, n_w, 0, launches + 1, 1, 0);

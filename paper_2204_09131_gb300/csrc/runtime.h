@@ -47,6 +47,7 @@ struct Lane {
     bool own_stream = false;
     DevBuf d_items, d_queue, d_out, d_nx, d_ny, d_c;
     DevBuf d_chain_desc, d_chain_steps, d_chain_state, d_chain_recomp, d_chain_out;
+    DevBuf d_gscratch;                 // sorted-path scratch of windows above kSortMax points
     HostBuf h_items, h_table;          // pinned staging: table + items; results
     bool queue_clean = false;          // d_queue holds zeroed work counters
     int slot_share = 4;                // quarters of the GPU's resident-CTA slots a launch

@@ -1033,14 +1033,18 @@ isycos_status round_begin(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *>
     rd.total = total;
     if (total == 0) return ISYCOS_OK;
     rd.res.resize(total);
+    bool present[kBatchKeys] = {false};
     int last_k = 0;
-    for (int kk = 1; kk < kBatchKeys; ++kk)
-        for (size_t q = 0; q < ms.size(); ++q)
-            if (!finished[q] && !rd.reqs[q].empty() && batch_key(*ms[q]) == kk) last_k = kk;
+    for (size_t q = 0; q < ms.size(); ++q)
+        if (!finished[q] && !rd.reqs[q].empty()) {
+            present[batch_key(*ms[q])] = true;
+            last_k = std::max(last_k, batch_key(*ms[q]));
+        }
     // Per (k, estimator) (machines of one call normally share them), split the requests into
-    // the batched list and the chains that the incremental kernel takes.
+    // the batched list and the chains that the incremental kernel takes.  Only keys with
+    // requests are visited: the last one's batch stays open in rd.batch / rd.where.
     for (int kk = 1; kk < kBatchKeys; ++kk) {
-        if (k > 0 && kk != k) continue;
+        if (!present[kk] || (k > 0 && kk != k)) continue;
         const int k_nb = kk % (kMaxK + 1), est = kk / (kMaxK + 1);
         std::vector<HostWindow> &batch = rd.batch;
         std::vector<size_t> &where = rd.where;

@@ -246,12 +246,15 @@ def test_sorted_path_equals_brute_force(ctx):
              (np.full(n, 2.5, np.float32), base), (np.round(base).astype(np.float32), -base)]
     sizes = [1025, 1500, 2048, 3001, 4096]
     starts = [11, 3000, 7000, 12000, 15000]
-    # windows of at most 1024 points run the sorted path in 256-thread CTAs
+    # windows of at most 1024 points run the sorted path in 256-thread CTAs; windows above
+    # 4096 points keep its scratch in global memory
     small_sizes = [257, 300, 513, 700, 1000, 1024, 64, 100]
     small_starts = [5, 2000, 4000, 6000, 9000, 12000, 15000, 17000]
+    big_sizes = [4097, 6000, 8192, 12001, 16384, 3000]
+    big_starts = [0, 13000, 1000, 7000, 3000, 16000]
     for ci, (xx, yy) in enumerate(cases):
         xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
-        for st_, sz_ in ((starts, sizes), (small_starts, small_sizes)):
+        for st_, sz_ in ((starts, sizes), (small_starts, small_sizes), (big_starts, big_sizes)):
             w = api.windows_array(xs, ys, st_, sz_)
             res2 = {}
             for opt in (1, 2):
@@ -269,6 +272,12 @@ def test_sorted_path_equals_brute_force(ctx):
         if ci < 3:
             r = O.ksg_window(xx[3000:4500], yy[3000:4500], 4, points=False)
             assert res[2][0]["s_psi"][1] == r["s_psi"] and res[2][0]["mi"][1] == r["mi"]
+        if ci == 0:   # one large window against the oracle
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 2)
+            got = api.isycos_mi_windows(ctx, api.windows_array(xs, ys, [1000], [8192]), 4)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+            r = O.ksg_window(xx[1000:9192], yy[1000:9192], 4, points=False)
+            assert got["s_psi"][0] == r["s_psi"] and got["mi"][0] == r["mi"]
         api.isycos_drop_series(ctx, xs)
         api.isycos_drop_series(ctx, ys)
 
@@ -373,9 +382,10 @@ def test_autotune_changes_speed_not_results(ctx):
     tune = api.isycos_autotune(ctx, 4)
     st1 = api.isycos_get_stats(ctx)
     assert st1["windows"] == st0["windows"] and st1["launches"] == st0["launches"]
-    assert set(tune["window_size"]) == {9, 10, 11, 12} and set(tune["sorted_buckets"]) <= {9, 10, 11, 12}
+    assert set(tune["window_size"]) == {9, 10, 11, 12, 13, 14}
+    assert set(tune["sorted_buckets"]) <= {9, 10, 11, 12, 13, 14}
     assert all(v > 0 for v in tune["brute_ms"].values()) and all(v > 0 for v in tune["sorted_ms"].values())
-    for b in (9, 10, 11, 12):
+    for b in (9, 10, 11, 12, 13, 14):
         assert (b in tune["sorted_buckets"]) == (tune["sorted_ms"][b] < tune["brute_ms"][b])
     after = api.isycos_mi_windows(ctx, w, 4)
     assert np.array_equal(before, after)
@@ -425,8 +435,8 @@ def test_sorted_path_repeats_bit_exact(ctx):
     xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
     rng = np.random.default_rng(11)
     lists = []
-    for lo, hi in ((257, 1024), (1025, 4096)):
-        sizes = rng.integers(lo, hi + 1, 600)
+    for lo, hi, cnt in ((257, 1024, 600), (1025, 4096, 600), (4097, 16384, 40)):
+        sizes = rng.integers(lo, hi + 1, cnt)
         starts = np.array([int(rng.integers(0, n - m)) for m in sizes])
         lists.append(api.windows_array(xs, ys, starts, sizes))
     try:

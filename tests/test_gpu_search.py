@@ -389,3 +389,55 @@ def test_speculation_depth_changes_work_not_results(ctx):
     assert launches[3] < launches[0]
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def test_serving_mixed_kinds_of_query(ctx):
+    """Served queries of every kind at once (TD, BU, selection, chunked, estimator 1), each
+    with its own parameters, return what the same query returns alone."""
+    api = _api()
+    pairs = []
+    for p in range(3):
+        x, y, _ = synth.planted_pair(4, 20 + p, 8000, len_lo=50, len_hi=1500)
+        pairs.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    kinds = [dict(mode=0, pruning=1), dict(mode=1, pruning=1, seed=3),
+             dict(mode=2, sel_partitions=8, sel_samples=3, seed=5), dict(mode=1, chunks=4),
+             dict(mode=0, estimator=1), dict(mode=1, estimator=1, pruning=1)]
+    jobs = []
+    for i, kind in enumerate(kinds * 2):
+        a, b = pairs[i % 3]
+        prm = dict(k=4, s_min=32, s_max=400, **kind)
+        jobs.append(((a, b, 100 * i, 8000 - 50 * i), prm))
+    tickets = [api.isycos_serve_submit(ctx, *q, prm) for q, prm in jobs]
+    res = {}
+    deadline = time.time() + 300
+    while len(res) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in res:
+                r = api.isycos_serve_poll(ctx, t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    for (q, prm), t in zip(jobs, tickets):
+        assert np.array_equal(api.isycos_search(ctx, *q, prm), res[t][0])
+
+
+def test_one_call_mixing_k_and_estimators(ctx):
+    """Queries with different k and estimators in one call (one lane, so that one round
+    carries several batches): every query returns what it returns alone."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    qs = [(xs, ys, 0, len(x), dict(k=k, s_min=32, s_max=256, mode=mode, estimator=est, pruning=1, seed=2))
+          for k in (3, 4) for est in (0, 1) for mode in (0, 1)]
+    alone = [api.isycos_search(ctx, *q[:4], q[4]) for q in qs]
+    try:
+        for lanes in (1, 3):
+            api.isycos_set_option(ctx, api.OPT_LANES, lanes)
+            got = api.isycos_search_queries(ctx, qs)
+            for a, g in zip(alone, got):
+                assert np.array_equal(a, g), lanes
+    finally:
+        api.isycos_set_option(ctx, api.OPT_LANES, 12)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
