@@ -355,7 +355,9 @@ private:
         void init(int min_side) {
             G = 64;
             lg = 6;
-            while (G < min_side) {
+            // (at most 256 x 256 cells, 2.6 MB: beyond that, cells of one round may share a
+            // slot, which costs a re-ask but never a wrong score)
+            while (G < min_side && G < 256) {
                 G <<= 1;
                 ++lg;
             }
