@@ -55,6 +55,14 @@ def parse():
                     help="time one kind of search query over --case-pairs pairs of --length "
                          "points instead of the default step (per-size launch statistics)")
     ap.add_argument("--lanes", type=int, default=0, help="ISYCOS_OPT_LANES (0: library default)")
+    ap.add_argument("--serving-case", action="store_true",
+                    help="the served form at scale: --serve-series resident series of "
+                         "--serve-length points, Poisson streams of --serve-queries queries at "
+                         "fractions --serve-rates of a measured capacity (p50/p99 latency)")
+    ap.add_argument("--serve-series", type=int, default=512)
+    ap.add_argument("--serve-length", type=int, default=1_000_000)
+    ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--serve-rates", default="0.3,0.7,1.0,1.3")
     ap.add_argument("--speculation", type=int, default=-1,
                     help="ISYCOS_OPT_SPECULATION (BU climbs asked ahead; -1: library default)")
     ap.add_argument("--plain", action="store_true", help="also time the one-window-per-launch form")
@@ -374,8 +382,86 @@ def search_case(args):
     api.isycos_destroy(ctx)
 
 
+def serving_case(args):
+    """Continuous batching at scale: random queries (random pair of the resident series, range
+    log-uniform in [1e3, length], s_max a power of two log-uniform in [256, 16384] clipped to
+    range / 2, SYCOS_TD and SYCOS_BU alternating) submitted as Poisson streams at fractions
+    of the capacity measured with the same kind of queries submitted all at once."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api, synth
+    ctx = api.isycos_create(0, 0)
+    n_pairs = max(1, args.serve_series // 2)
+    ids = []
+    for p in range(n_pairs):
+        x, y, _ = synth.planted_pair(4, p, args.serve_length)
+        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    api.isycos_autotune(ctx, PARAMS["k"])
+    length = args.serve_length
+
+    def make_queries(n, seed):
+        rng = np.random.default_rng(seed)
+        qs = []
+        for i in range(n):
+            a, b = ids[int(rng.integers(0, len(ids)))]
+            span = int(np.exp(rng.uniform(np.log(1000), np.log(length))))
+            lo = int(rng.integers(0, length - span + 1))
+            s_max = int(2 ** rng.integers(8, 15))
+            s_max = max(64, min(s_max, span // 2))
+            qs.append((a, b, lo, lo + span, dict(PARAMS, s_max=s_max, mode=int(i % 2))))
+        return qs
+
+    def run(qs, gaps):
+        tickets, done = [], {}
+        start = time.perf_counter()
+        nxt = start
+        for q, g in zip(qs, gaps):
+            nxt += g
+            while time.perf_counter() < nxt:
+                time.sleep(0.0002)
+            tickets.append(api.isycos_serve_submit(ctx, *q[:4], q[4]))
+            for t in tickets[-64:]:
+                if t not in done:
+                    r = api.isycos_serve_poll(ctx, t)
+                    if r is not None:
+                        done[t] = r[1]
+        while len(done) < len(tickets):
+            for t in tickets:
+                if t not in done:
+                    r = api.isycos_serve_poll(ctx, t)
+                    if r is not None:
+                        done[t] = r[1]
+            time.sleep(0.001)
+        wall = time.perf_counter() - start
+        lat = np.array([done[t] for t in tickets])
+        return {"queries": len(qs), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                "throughput_qps": round(len(qs) / wall, 2)}
+
+    cal = run(make_queries(min(256, args.serve_queries), 1), [0.0] * min(256, args.serve_queries))
+    capacity = cal["throughput_qps"]
+    sweep = []
+    for f in [float(v) for v in args.serve_rates.split(",")]:
+        qs = make_queries(args.serve_queries, 100 + int(f * 100))
+        gaps = np.random.default_rng(7).exponential(1.0 / (f * capacity), len(qs))
+        r = run(qs, gaps)
+        r["rate_fraction"] = f
+        r["arrival_qps"] = round(f * capacity, 2)
+        sweep.append(r)
+    st = api.isycos_get_stats(ctx)
+    line = {"serving_case": True, "series": 2 * n_pairs, "length": length,
+            "capacity_qps": capacity, "calibration": cal, "sweep": sweep,
+            "queries_done": st["queries_done"]}
+    print(json.dumps(line), flush=True)
+    api.isycos_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.serving_case:
+        return serving_case(args)
     if args.search_case:
         return search_case(args)
     if args.impl == "reference":
@@ -478,7 +564,10 @@ def main():
             "kernel": "ksg_batched_kernel", "kernel_ms_per_step": round(kms / args.steps, 3),
             "kernel_share_of_step": round(kms / total_ms, 4) if total_ms else None,
             "peak_basis": "%d SMs x 4 warp-instr/clk x 32 lanes x %.0f MHz (median SM clock "
-                          "sampled during the timed region)" % (n_sm, f_mhz)}
+                          "sampled during the timed region)" % (n_sm, f_mhz),
+            "work_basis": "brute-force-equivalent: 11 lane-ops per ordered pair m(m-1) of every "
+                          "evaluated window, over the union of the batched kernel's launch "
+                          "intervals (windows on the sorted path do less work than that)"}
 
     serving = None
     if rank == 0 and not args.no_serving:

@@ -53,6 +53,8 @@ typedef int32_t isycos_status;
 #define ISYCOS_MAX_K 8
 /* Largest LAHC idle limit T_maxIdle of SYCOS_BU (its rings reach N_{T_maxIdle + 1}). */
 #define ISYCOS_MAX_IDLE 64
+/* Most series resident in one context at a time. */
+#define ISYCOS_MAX_SERIES (1 << 20)
 
 typedef struct isycos_ctx isycos_ctx;
 
@@ -164,7 +166,9 @@ void isycos_params_default(isycos_params *p);
 /* Make a series resident (Def. 3.1): copies n float32 values from `data` (device memory if
  * on_device != 0, else host memory) into library-owned device memory and returns its id.
  * Non-finite values are rejected (E_INVAL): the estimator's distances need finite input.
- * Errors: E_INVAL (n < 1, NULL, non-finite), E_NOMEM (budget), E_CUDA. */
+ * May be called while served queries run (they only read the series they named).
+ * Errors: E_INVAL (n < 1, NULL, non-finite), E_NOMEM (budget, or ISYCOS_MAX_SERIES series
+ * resident), E_CUDA. */
 isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n,
                                 int32_t on_device, int32_t *series_id);
 

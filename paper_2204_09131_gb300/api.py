@@ -347,16 +347,21 @@ def isycos_serve_submit(ctx, xs: int, ys: int, t_begin: int, t_end: int, params=
     return t.value
 
 
-def isycos_serve_poll(ctx, ticket: int, cap: int = 1 << 16):
-    """Returns None while pending, else (windows, latency_ms)."""
-    out = np.empty(cap, dtype=RESULT_DTYPE)
-    n = ctypes.c_int64()
-    lat = ctypes.c_double()
-    st = lib().isycos_serve_poll(ctx, ticket, _ptr(out), cap, ctypes.byref(n), ctypes.byref(lat))
-    if st == PENDING:
-        return None
-    _check(ctx, st)
-    return out[:n.value].copy(), lat.value
+def isycos_serve_poll(ctx, ticket: int, cap: int = 1024):
+    """Returns None while pending, else (windows, latency_ms).  A result larger than `cap`
+    is fetched again with the size the library reports."""
+    while True:
+        out = np.empty(cap, dtype=RESULT_DTYPE)
+        n = ctypes.c_int64()
+        lat = ctypes.c_double()
+        st = lib().isycos_serve_poll(ctx, ticket, _ptr(out), cap, ctypes.byref(n), ctypes.byref(lat))
+        if st == PENDING:
+            return None
+        if st == E_TRUNC and n.value > cap:
+            cap = int(n.value)
+            continue
+        _check(ctx, st)
+        return out[:n.value].copy(), lat.value
 
 
 def isycos_serve_cancel(ctx, ticket: int):

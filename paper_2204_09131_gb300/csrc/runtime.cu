@@ -460,6 +460,10 @@ isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budge
     if (device < 0 || device >= ndev) return ISYCOS_E_INVAL;
     isycos_ctx *ctx = new isycos_ctx();
     ctx->device = device;
+    // the series tables never reallocate: serving threads read them while the caller adds
+    // series
+    ctx->series_ptr.reserve(kMaxSeries);
+    ctx->series_len.reserve(kMaxSeries);
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
@@ -587,6 +591,11 @@ isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, i
             break;
         }
     if (id < 0) {
+        if (ctx->series_ptr.size() >= (size_t)kMaxSeries) {
+            cudaFree(d);
+            ctx->used -= bytes;
+            return fail(ctx, ISYCOS_E_NOMEM, "put_series: %d series resident", kMaxSeries);
+        }
         id = (int32_t)ctx->series_ptr.size();
         ctx->series_ptr.push_back(nullptr);
         ctx->series_len.push_back(0);

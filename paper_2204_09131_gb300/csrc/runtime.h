@@ -20,6 +20,7 @@ namespace isy {
 // Lane indices: searches use 0 .. kMaxLanes - 1 (default priority) and kPrioLaneBase + i
 // (highest stream priority, for latency-bound searches); serving workers kServeLaneBase + w.
 constexpr int kMaxLanes = 16;
+constexpr int kMaxSeries = ISYCOS_MAX_SERIES;   // resident series per context
 constexpr int kServeLaneBase = 32;
 constexpr int kPrioLaneBase = 48;
 constexpr int kLaneSlots = 64;

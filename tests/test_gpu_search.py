@@ -441,3 +441,32 @@ def test_one_call_mixing_k_and_estimators(ctx):
         api.isycos_set_option(ctx, api.OPT_LANES, 12)
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def test_series_added_while_queries_are_served(ctx):
+    """The caller may add series while served queries run (the library's serving threads
+    read the series tables concurrently); every result still equals the query alone."""
+    api = _api()
+    x, y, _ = synth.planted_pair(4, 40, 20000, len_lo=50, len_hi=2000)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    prm = dict(k=4, s_min=32, s_max=512, mode=1, pruning=1, seed=4)
+    qs = [(xs, ys, 1000 * i, 20000 - 500 * i) for i in range(8)]
+    tickets = [api.isycos_serve_submit(ctx, *q, prm) for q in qs]
+    extra = []
+    for i in range(300):   # grows the series tables while the queries run
+        z = synth.normal(synth.seed_for(41, i), 64).astype(np.float32)
+        extra.append(api.isycos_put_series(ctx, z))
+    res = {}
+    deadline = time.time() + 300
+    while len(res) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in res:
+                r = api.isycos_serve_poll(ctx, t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    for q, t in zip(qs, tickets):
+        assert np.array_equal(api.isycos_search(ctx, *q, prm), res[t][0])
+    for e in extra:
+        api.isycos_drop_series(ctx, e)
