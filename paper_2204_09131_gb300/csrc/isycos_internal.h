@@ -12,8 +12,12 @@ constexpr int kMaxM = ISYCOS_MAX_M;
 constexpr int kMaxK = ISYCOS_MAX_K;
 constexpr int kTableN = kMaxM + 2;      // psi_fx / log_fx entries 0 .. kMaxM + 1
 constexpr int kBuckets = 15;            // size buckets: m <= 2^b, b = 0 .. 14, stored largest first
-constexpr int kPoints = 2;              // points per thread in the brute-force kernels
+// Points per lane in the CTA jobs of the brute-force kernels.  One point per lane spreads a
+// window over twice as many warps as two would, which shortens the dependent chains of a
+// launch of small windows (the latency of a SYCOS_BU round) at the same total work.
+constexpr int kPoints = 1;
 constexpr int kBlockPts = 32 * kPoints; // points per warp block
+constexpr int kWarpSlicePts = 64;       // staging slice of one warp in the small-window phase
 
 // One resolved window: device pointers to its first X and Y values.  32 bytes.
 struct WorkItem {
@@ -30,6 +34,8 @@ struct WorkItem {
 // slots >= kSmallSlot) are taken one per warp, with no CTA barrier, once a CTA runs out of
 // CTA jobs.
 constexpr int kSmallSlot = kBuckets - 7;   // m <= 2^6
+static_assert((1 << (kBuckets - 1 - kSmallSlot)) <= kWarpSlicePts,
+              "a warp's staging slice holds the largest single-warp window");
 struct BucketTable {
     int32_t total_jobs;          // CTA jobs
     int32_t n_items;
@@ -165,7 +171,7 @@ __host__ __device__ inline size_t sorted_smem(int m) { return sorted_off(m) + so
 // largest window that takes the sorted path (0: none).
 inline size_t batched_smem(int max_m, int nt, int max_sorted = 0) {
     size_t a = (size_t)max_m * 8;
-    size_t b = (size_t)nt * kPoints * 8;   // all slots of the small-window buckets
+    size_t b = (size_t)(nt / 32) * kWarpSlicePts * 8;   // the warps' small-window slices
     size_t c = max_sorted > 0 ? sorted_smem(max_sorted) : 0;
     return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }

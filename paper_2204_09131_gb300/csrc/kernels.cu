@@ -22,8 +22,8 @@
 // (taken by a warp only if one of its points needs it).
 //
 // Layout: the window's values are staged in shared memory as float2 (x, y); each lane owns
-// kPoints points of a 64-point block and reads (x_j, y_j) as a broadcast, so every shared
-// load serves 32 * kPoints pairs.  Work: m (m - 1) pairs per pass; no tensor cores (the path
+// P points of a block of 32 P points and reads (x_j, y_j) as a broadcast, so every shared
+// load serves 32 P pairs.  Work: m (m - 1) pairs per pass; no tensor cores (the path
 // is compare-and-count work on the FP32/INT pipes).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,23 +43,24 @@ __device__ __forceinline__ long long warp_sum64(long long v) {
     return v;
 }
 
-// Stable insertion of (d, j) into the ascending list bd/bj of K1 entries, given that d is
-// strictly smaller than the last entry: the last entry is replaced and bubbled toward the
-// front while strictly smaller than its predecessor.
+// Stable insertion of (d, j) into the ascending list bd/bj of K1 entries.  Every entry is
+// computed from the old list at once: position r takes its predecessor when that is larger
+// than d (the tail moves back one), d itself at the first position holding a larger value
+// (so d lands after equal entries: candidates arrive in increasing j), else stays.  The
+// dependent depth is one compare and two selects, against K1 - 1 compare-swap stages of a
+// bubbling insertion; with d >= the last entry nothing changes.
 template <int K1>
 __device__ __forceinline__ void list_insert(float (&bd)[K1], int (&bj)[K1], float d, int j) {
-    bd[K1 - 1] = d;
-    bj[K1 - 1] = j;
+    bool c[K1];
+#pragma unroll
+    for (int r = 0; r < K1; ++r) c[r] = bd[r] > d;
 #pragma unroll
     for (int r = K1 - 1; r > 0; --r) {
-        const bool sw = bd[r] < bd[r - 1];
-        const float a0 = bd[r - 1], a1 = bd[r];
-        const int b0 = bj[r - 1], b1 = bj[r];
-        bd[r - 1] = sw ? a1 : a0;
-        bd[r] = sw ? a0 : a1;
-        bj[r - 1] = sw ? b1 : b0;
-        bj[r] = sw ? b0 : b1;
+        bd[r] = c[r - 1] ? bd[r - 1] : (c[r] ? d : bd[r]);
+        bj[r] = c[r - 1] ? bj[r - 1] : (c[r] ? j : bj[r]);
     }
+    bd[0] = c[0] ? d : bd[0];
+    bj[0] = c[0] ? j : bj[0];
 }
 
 // Canonical binary64 evaluation of the window scalars from the exact integer sums.
@@ -284,20 +285,20 @@ __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all
         }
 }
 
+// The same insertion under the lexicographic order of (d, j), for candidates that arrive
+// out of index order.
 template <int K1>
 __device__ __forceinline__ void insert_lex(float (&bd)[K1], int (&bj)[K1], float d, int j) {
-    bd[K1 - 1] = d;
-    bj[K1 - 1] = j;
+    bool c[K1];
+#pragma unroll
+    for (int r = 0; r < K1; ++r) c[r] = bd[r] > d || (bd[r] == d && bj[r] > j);
 #pragma unroll
     for (int r = K1 - 1; r > 0; --r) {
-        const bool sw = bd[r] < bd[r - 1] || (bd[r] == bd[r - 1] && bj[r] < bj[r - 1]);
-        const float a0 = bd[r - 1], a1 = bd[r];
-        const int b0 = bj[r - 1], b1 = bj[r];
-        bd[r - 1] = sw ? a1 : a0;
-        bd[r] = sw ? a0 : a1;
-        bj[r - 1] = sw ? b1 : b0;
-        bj[r] = sw ? b0 : b1;
+        bd[r] = c[r - 1] ? bd[r - 1] : (c[r] ? d : bd[r]);
+        bj[r] = c[r - 1] ? bj[r - 1] : (c[r] ? j : bj[r]);
     }
+    bd[0] = c[0] ? d : bd[0];
+    bj[0] = c[0] ? j : bj[0];
 }
 
 __host__ __device__ inline int pow2_ceil(int m) {
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                          a.psi_fx, a.log_fx, a.inv_k);
     }
     // Small windows (m <= 64): one warp each, staged in the warp's own slice, no CTA barrier.
-    float2 *ws = tile + warp * kBlockPts;
+    float2 *ws = tile + warp * kWarpSlicePts;
     const int first = T->small_first, last = T->n_items;
     // lane r keeps the sums of the r-th pending window of this warp; the lanes finish up to
     // 32 windows together

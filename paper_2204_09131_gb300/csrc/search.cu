@@ -344,14 +344,18 @@ private:
     // its coordinates kept to tell it from the cells that share the slot), so it follows the
     // search along the series without copying.
     struct GridCache {
+        // One record per slot, so that a lookup touches one cache line.
+        struct Slot {
+            int64_t ka = 0, kb = 0;   // the cell that owns the slot
+            Val val{0.0, 0.0};
+            uint32_t tag = 0;         // == gen: val holds the score of cell (ka, kb)
+            uint32_t asked = 0;       // round in which (ka, kb) was last asked
+        };
         int G = 64, lg = 6;
         int64_t bs = 0, be = 0, d = 1;
         uint32_t gen = 1;
         bool valid = false;
-        std::vector<Val> val;
-        std::vector<uint32_t> tag;     // == gen: val holds the score of cell (ka, kb)
-        std::vector<uint32_t> asked;   // round in which (ka, kb) was last asked
-        std::vector<int64_t> ka, kb;
+        std::vector<Slot> cell;
         void init(int min_side) {
             G = 64;
             lg = 6;
@@ -361,11 +365,7 @@ private:
                 G <<= 1;
                 ++lg;
             }
-            val.assign((size_t)G * G, Val{0.0, 0.0});
-            tag.assign((size_t)G * G, 0);
-            asked.assign((size_t)G * G, 0);
-            ka.assign((size_t)G * G, 0);
-            kb.assign((size_t)G * G, 0);
+            cell.assign((size_t)G * G, Slot{});
         }
         bool on_lattice(int64_t ws, int64_t we, int64_t delta) const {
             return valid && delta == d && (ws - bs) % d == 0 && (we - be) % d == 0;
@@ -385,31 +385,37 @@ private:
             return ((size_t)(a & (G - 1)) << lg) | (size_t)(b & (G - 1));
         }
         bool get(int64_t a, int64_t b, Val *v) const {
-            const size_t i = slot(a, b);
-            if (tag[i] != gen || ka[i] != a || kb[i] != b) return false;
-            *v = val[i];
+            const Slot &c = cell[slot(a, b)];
+            if (c.tag != gen || c.ka != a || c.kb != b) return false;
+            *v = c.val;
             return true;
         }
-        bool known(int64_t a, int64_t b) const {
-            const size_t i = slot(a, b);
-            return tag[i] == gen && ka[i] == a && kb[i] == b;
+        // (a, b) has a score, or was asked in round `round`
+        bool known_or_asked(int64_t a, int64_t b, uint32_t round) const {
+            const Slot &c = cell[slot(a, b)];
+            return c.ka == a && c.kb == b && (c.tag == gen || c.asked == round);
+        }
+        // the slot of (a, b) holds another cell asked in round `round`
+        bool taken(int64_t a, int64_t b, uint32_t round) const {
+            const Slot &c = cell[slot(a, b)];
+            return c.asked == round && (c.ka != a || c.kb != b);
         }
         // mark (a, b) as asked in round `round`; false if it already was
         bool mark(int64_t a, int64_t b, uint32_t round) {
-            const size_t i = slot(a, b);
-            if (asked[i] == round && ka[i] == a && kb[i] == b) return false;
-            if (ka[i] != a || kb[i] != b) tag[i] = 0;   // the slot now belongs to (a, b)
-            asked[i] = round;
-            ka[i] = a;
-            kb[i] = b;
+            Slot &c = cell[slot(a, b)];
+            if (c.asked == round && c.ka == a && c.kb == b) return false;
+            if (c.ka != a || c.kb != b) c.tag = 0;   // the slot now belongs to (a, b)
+            c.asked = round;
+            c.ka = a;
+            c.kb = b;
             return true;
         }
         void put(int64_t a, int64_t b, const Val &v) {
-            const size_t i = slot(a, b);
-            val[i] = v;
-            tag[i] = gen;
-            ka[i] = a;
-            kb[i] = b;
+            Slot &c = cell[slot(a, b)];
+            c.val = v;
+            c.tag = gen;
+            c.ka = a;
+            c.kb = b;
         }
     };
     // Scores of noise-test extension windows (start, size): a small direct-mapped cache.
@@ -508,10 +514,8 @@ private:
         auto visit = [&](int a, int b) {
             int64_t ts, te;
             if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
-            if (grid_.known(ac + a, bc + b)) return;                 // evaluated earlier
-            const size_t i = grid_.slot(ac + a, bc + b);
-            if (grid_.asked[i] == round_ && grid_.ka[i] == ac + a && grid_.kb[i] == bc + b)
-                return;                                               // asked in this round
+            // evaluated earlier, or asked in this round
+            if (grid_.known_or_asked(ac + a, bc + b, round_)) return;
             ask_cell(ac + a, bc + b, ts, te, kDestCell, r, chain);
         };
         for (int b = -r; b <= r; ++b) visit(-r, b);
@@ -579,11 +583,9 @@ private:
         }
     }
     void spec_cell(int64_t a, int64_t b, int64_t ts, int64_t te) {
-        if (grid_.known(a, b)) return;
-        const size_t i = grid_.slot(a, b);
-        if (grid_.asked[i] == round_ && grid_.ka[i] == a && grid_.kb[i] == b) return;
+        if (grid_.known_or_asked(a, b, round_)) return;
         // never take a slot that holds a cell asked in this round
-        if (grid_.asked[i] == round_) return;
+        if (grid_.taken(a, b, round_)) return;
         ask_cell(a, b, ts, te, kDestCell, -1, -1);
     }
     void spec_ext(int64_t ts, int64_t te) {
