@@ -99,12 +99,9 @@ cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
 cudaError_t launch_prep(const PrepArgs &a, cudaStream_t st, int *launches);
 cudaError_t launch_check_finite(const float *d, int64_t n, int32_t *flag, cudaStream_t st);
 
+__host__ __device__ inline int size_bucket(int m);
 // Bucket of a window size: smallest b with m <= 2^b; slot q = kBuckets - 1 - b (largest first).
-inline int bucket_slot(int m) {
-    int b = 0;
-    while ((1 << b) < m) ++b;
-    return kBuckets - 1 - b;
-}
+inline int bucket_slot(int m) { return kBuckets - 1 - size_bucket(m); }
 
 // Warps per item for bucket slot q in a CTA of nt threads.
 __host__ __device__ inline int warps_per_item(int q, int nt) {
@@ -151,9 +148,12 @@ constexpr int kSortMax = 4096;
 constexpr uint32_t kSortBuckets = (1u << 9) | (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14);
 constexpr uint32_t kDefaultSortBuckets = (1u << 11) | (1u << 12) | (1u << 13) | (1u << 14);
 __host__ __device__ inline int size_bucket(int m) {   // smallest b with m <= 2^b
-    int b = 0;
-    while ((1 << b) < m) ++b;
-    return b;
+    if (m <= 1) return 0;
+#ifdef __CUDA_ARCH__
+    return 32 - __clz(m - 1);
+#else
+    return 32 - __builtin_clz((unsigned)(m - 1));
+#endif
 }
 
 // Sorted path layout in shared memory after the window's m float2 values: the sort keys

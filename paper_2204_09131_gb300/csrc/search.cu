@@ -245,7 +245,6 @@ public:
                 }
                 ws_ = c_;
                 we_ = c_ + prm.s_min - 1;
-                invalidate_rings();
                 // scores are pure functions of the window: keep the cells of earlier climbs
                 // when this start lies on their lattice
                 if (!grid_.on_lattice(ws_, we_, prm.delta_bu)) {
@@ -259,7 +258,7 @@ public:
                 if (!grid_.get(ac, bc, &start_val_)) ask_cell(ac, bc, ws_, we_, kDestStart, -1, -1);
                 if (prm.t_max_idle >= 0 && prm.max_steps > 0)
                     for (int rr = 1; rr <= std::min(prm.t_max_idle + 1, spec_depth()); ++rr)
-                        ask_ring(rr, false, false);
+                        ask_ring(rr, false, false, false);
                 phase_ = kWaitStart;
                 if (asked_.empty()) continue;
                 speculate_next_climbs();
@@ -270,8 +269,9 @@ public:
                 continue;
             }
             if (phase_ == kRing) {
-                // After a rejection the window stays put and the rings N_r .. N_{T+1} are
-                // evaluated until one improves: ask for all of them at once.
+                // Some score of ring N_r is missing.  After a rejection the window stays put
+                // and the rings N_r .. N_{T+1} are evaluated until one improves: ask for all
+                // of them at once.
                 const int r = t_idle_ + 1;
                 int r_last = t_idle_ >= 1 ? prm.t_max_idle + 1 : r;
                 // Small windows are cheap on the GPU and every round trip costs the same: also
@@ -279,23 +279,22 @@ public:
                 // climb moves by one delta and the remaining rings when it does not.
                 r_last = std::max(r_last, std::min(prm.t_max_idle + 1, spec_depth()));
                 const size_t before = asked_.size();
-                ask_ring(r, dropped_[0], dropped_[1]);
+                ask_ring(r, dropped_[0], dropped_[1], stuck_);
                 // speculate only when this step needs a round trip anyway
                 if (asked_.size() > before) {
-                    for (int rr = r + 1; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1]);
+                    for (int rr = r + 1; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1], false);
                     speculate_next_climbs();
                 }
+                // (a ring whose scores are all cached has nothing to ask; if its decision
+                // still finds one missing, the next ask ignores the caches)
+                stuck_ = asked_.size() == before;
                 phase_ = kDecide;
                 if (asked_.empty()) continue;
                 break;
             }
             if (phase_ == kDecide) {
-                const int r = t_idle_ + 1;
-                if (!ring_ready(r)) {
-                    phase_ = kRing;
-                    continue;
-                }
-                decide(r);
+                if (!decide(t_idle_ + 1)) phase_ = kRing;
+                else stuck_ = false;
                 continue;
             }
         }
@@ -311,11 +310,11 @@ public:
                 if (d.kind == kDestStart) start_val_ = v;
                 grid_.put(d.a, d.b, v);
             } else if (d.kind == kDestExt) {
-                if (d.r >= 0) {
-                    rings_[d.r].ext_val[d.side] = v;
-                    rings_[d.r].ext_have[d.side] = 1;
-                }
                 ext_.put(d.a, d.b, v);
+                // the extension windows of the rings asked for the next decisions are also
+                // kept by ring and side: the direct-mapped cache may lose one of them to
+                // another window of the same round
+                if (d.r >= 0) ring_ext_[(size_t)(2 * d.r + d.side)] = RingExt{d.a, d.b, v};
             }
         }
     }
@@ -324,7 +323,8 @@ public:
         c_ = t_begin;
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
-        rings_.resize((size_t)prm.t_max_idle + 2);
+        cand_.reserve((size_t)8 * (prm.t_max_idle + 1));
+        ring_ext_.assign((size_t)2 * (prm.t_max_idle + 2), RingExt{});
         // the cells one round asks span T_maxIdle + 1 cells around the window and the windows
         // of the climbs asked ahead, s_min / delta cells apart: the direct-mapped array must
         // be wider than that span so that they do not evict one another
@@ -455,14 +455,23 @@ private:
             x.v = v;
         }
     };
-    // Ring N_r asked around the centre (cs, ce).  Its windows' scores are cells of the grid
-    // cache; the noise-test extension windows are kept here.
-    struct Ring {
-        bool asked = false;
-        int64_t cs = 0, ce = -1;
-        Val ext_val[2];
-        char ext_have[2] = {0, 0};
+    // Candidates of the ring being decided, in the decision order.
+    struct Cand {
+        int64_t ts, te;
+        Val v;
     };
+    // Score of the extension window (s, m) last delivered for a ring and side.
+    struct RingExt {
+        int64_t s = -1, m = 0;
+        Val v{0.0, 0.0};
+    };
+    bool ext_score(int r, int side, int64_t s, int64_t m, Val *v) const {
+        if (ext_.get(s, m, v)) return true;
+        const RingExt &e = ring_ext_[(size_t)(2 * r + side)];
+        if (e.s != s || e.m != m) return false;
+        *v = e.v;
+        return true;
+    }
 
     void ask_cell(int64_t a, int64_t b, int64_t ts, int64_t te, int kind, int r, int32_t chain) {
         asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), chain, false});
@@ -472,15 +481,6 @@ private:
     void ask_ext(int64_t ts, int64_t te, int r, int side) {
         asked_.push_back(WinReq{ts, (int32_t)(te - ts + 1), -1, false});
         dest_.push_back(Dest{kDestExt, r, side, ts, te - ts + 1});
-    }
-
-    void invalidate_rings() {
-        for (Ring &g : rings_) g.asked = false;
-    }
-
-    bool ring_ready(int r) const {
-        const Ring &g = rings_[r];
-        return g.asked && g.cs == ws_ && g.ce == we_;
     }
 
     // A candidate of ring N_r around (ws_, we_) passes the filters of the search.
@@ -501,12 +501,7 @@ private:
     // Ask for ring N_r around the current window: the candidates walked along the perimeter
     // from (-r, -r) so that consecutive windows differ by one delta at one end (the current
     // window starts the chain), then the noise-test extension windows.
-    void ask_ring(int r, bool drop_left, bool drop_right) {
-        Ring &g = rings_[r];
-        g.asked = true;
-        g.cs = ws_;
-        g.ce = we_;
-        g.ext_have[0] = g.ext_have[1] = 0;
+    void ask_ring(int r, bool drop_left, bool drop_right, bool all) {
         const int32_t chain = next_chain_++;
         const size_t first = asked_.size();
         int64_t ac, bc;
@@ -515,7 +510,7 @@ private:
             int64_t ts, te;
             if (!keep(a, b, r, drop_left, drop_right, &ts, &te)) return;
             // evaluated earlier, or asked in this round
-            if (grid_.known_or_asked(ac + a, bc + b, round_)) return;
+            if (!all && grid_.known_or_asked(ac + a, bc + b, round_)) return;
             ask_cell(ac + a, bc + b, ts, te, kDestCell, r, chain);
         };
         for (int b = -r; b <= r; ++b) visit(-r, b);
@@ -535,10 +530,7 @@ private:
             for (int sd = 0; sd < 2; ++sd) {
                 if (!keep(sd == 0 ? -r : 0, sd == 0 ? 0 : r, r, drop_left, drop_right, &ts, &te)) continue;
                 Val v;
-                if (ext_.get(es[sd], ee[sd] - es[sd] + 1, &v)) {
-                    g.ext_val[sd] = v;
-                    g.ext_have[sd] = 1;
-                } else {
+                if (all || !ext_.get(es[sd], ee[sd] - es[sd] + 1, &v)) {
                     ext_.mark(es[sd], ee[sd] - es[sd] + 1, round_);
                     ask_ext(es[sd], ee[sd], r, sd);
                 }
@@ -563,12 +555,18 @@ private:
             Val seen;
             if (spec_starts_.find((uint64_t)c, &seen)) continue;   // asked in an earlier round
             spec_starts_.put((uint64_t)c, Val{0.0, 0.0});
+            // When the start one delta earlier was asked ahead too, its square of cells
+            // (offsets up to `depth` around it) holds every cell of this one but those at
+            // offset +depth in a or b: ask only those (a cell the cache has lost since is asked
+            // again when a decision needs it).
+            const bool near = spec_starts_.find((uint64_t)(c - d), &seen);
             int64_t ac, bc;
             grid_.centre(cs, ce, &ac, &bc);
-            spec_cell(ac, bc, cs, ce);
+            if (!near) spec_cell(ac, bc, cs, ce);
             for (int r = 1; r <= depth; ++r) {
                 for (int a = -r; a <= r; ++a)
                     for (int b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
+                        if (near && a != depth && b != depth) continue;
                         const int64_t ts = cs + a * d, te = ce + b * d, mm = te - ts + 1;
                         if (mm < prm.s_min || mm > prm.s_max) continue;
                         if (ts < t_begin || te > t_end - 1 || ts <= last_end_) continue;
@@ -620,57 +618,58 @@ private:
             end_climb();
     }
 
-    // One LAHC step on ring N_r (Algorithm 2), with the current dropped directions.
-    void decide(int r) {
-        const Ring &g = rings_[r];
+    // One LAHC step on ring N_r (Algorithm 2), with the current dropped directions, read from
+    // the score caches.  Returns false, with nothing changed, when a score it needs is not
+    // cached (not asked yet, or its slot was taken by another window since).
+    bool decide(int r) {
         int64_t ac, bc;
         grid_.centre(ws_, we_, &ac, &bc);
-        bool have = false;
-        int64_t bs = 0, be = 0;
-        Val bv{0.0, 0.0};
-        double pure_sc[2] = {0.0, 0.0};
-        bool pure_found[2] = {false, false};
+        cand_.clear();
+        int pure[2] = {-1, -1};   // candidates (-r, 0) and (0, r): the pure extensions
         for (int64_t a = -r; a <= r; ++a)
             // the perimeter of the square, b ascending within each a
             for (int64_t b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
                 int64_t ts, te;
                 if (!keep(a, b, r, dropped_[0], dropped_[1], &ts, &te)) continue;
                 Val v;
-                if (!grid_.get(ac + a, bc + b, &v)) {
-                    // only when another cell took the slot since the ring was asked: ask it
-                    // again
-                    phase_ = kRing;
-                    rings_[r].asked = false;
-                    return;
-                }
-                count(te - ts + 1);
-                if (!have || v.score > bv.score) {        // first maximum wins
-                    have = true;
-                    bs = ts;
-                    be = te;
-                    bv = v;
-                }
-                if (a == -r && b == 0) {
-                    pure_found[0] = true;
-                    pure_sc[0] = v.score;
-                }
-                if (a == 0 && b == r) {
-                    pure_found[1] = true;
-                    pure_sc[1] = v.score;
-                }
+                if (!grid_.get(ac + a, bc + b, &v)) return false;
+                if (a == -r && b == 0) pure[0] = (int)cand_.size();
+                if (a == 0 && b == r) pure[1] = (int)cand_.size();
+                cand_.push_back(Cand{ts, te, v});
             }
+        // the noise test's extension windows (Def. 6.2): the r delta points added on that side
+        const bool test = prm.pruning && (int64_t)r * prm.delta_bu >= prm.k + 1;
+        Val ext[2];
+        if (test) {
+            const int64_t span = (int64_t)r * prm.delta_bu;
+            const int64_t es[2] = {ws_ - span, we_ + 1};
+            for (int sd = 0; sd < 2; ++sd)
+                if (pure[sd] >= 0 && !ext_score(r, sd, es[sd], span, &ext[sd])) return false;
+        }
+        // every score is at hand: the step
+        bool have = false;
+        int64_t bs = 0, be = 0;
+        Val bv{0.0, 0.0};
+        for (const Cand &c : cand_) {
+            count(c.te - c.ts + 1);
+            if (!have || c.v.score > bv.score) {        // first maximum wins
+                have = true;
+                bs = c.ts;
+                be = c.te;
+                bv = c.v;
+            }
+        }
         if (prm.pruning) {
-            for (int s = 0; s < 2; ++s) {
-                if (!pure_found[s]) continue;
+            for (int sd = 0; sd < 2; ++sd) {
+                if (pure[sd] < 0) continue;
                 bool noise = false;
-                if ((int64_t)r * prm.delta_bu >= prm.k + 1) {
-                    const Val &e = g.ext_val[s];
+                if (test) {
                     count((int64_t)r * prm.delta_bu);
                     // Def. 6.2 with w = current window, w' = extension, w'' = the neighbour.
-                    noise = (Iw_ > 0.0) && (e.score < prm.tau) && (pure_sc[s] < Iw_);
+                    noise = (Iw_ > 0.0) && (ext[sd].score < prm.tau) && (cand_[pure[sd]].v.score < Iw_);
                 }
-                run_[s] = noise ? run_[s] + 1 : 0;
-                if (run_[s] >= prm.p) dropped_[s] = true;
+                run_[sd] = noise ? run_[sd] + 1 : 0;
+                if (run_[sd] >= prm.p) dropped_[sd] = true;
             }
         }
         const int v = (int)(splitmix64_at(prm.seed, (climb_ << 32) + step_ + 1) % (uint64_t)prm.h);
@@ -689,6 +688,7 @@ private:
             phase_ = kDecide;
         else
             end_climb();
+        return true;
     }
 
     void end_climb() {
@@ -717,7 +717,9 @@ private:
     uint64_t step_ = 0, climb_ = 0;
     int run_[2] = {0, 0};
     bool dropped_[2] = {false, false};
-    std::vector<Ring> rings_;
+    std::vector<Cand> cand_;
+    std::vector<RingExt> ring_ext_;
+    bool stuck_ = false;
     std::vector<Dest> dest_;
     GridCache grid_;
     ExtCache ext_;
@@ -1058,42 +1060,40 @@ isycos_status round_begin(isycos_ctx *ctx, Lane &L, std::vector<SearchMachine *>
         for (size_t q = 0; q < ms.size(); ++q) {
             if (finished[q] || rd.reqs[q].empty() || batch_key(*ms[q]) != kk) continue;
             const auto &rq = rd.reqs[q];
-            int32_t n_groups = 0;
-            for (const WinReq &r : rq) n_groups = std::max(n_groups, r.chain + 1);
-            thread_local std::vector<char> in_chain;
-            in_chain.assign(rq.size(), 0);
             // the incremental kernel implements the second estimator only
-            if (ctx->opt_incremental == 0 || est != 0) n_groups = 0;
-            thread_local std::vector<std::vector<size_t>> groups;
-            if (groups.size() < (size_t)n_groups) groups.resize((size_t)n_groups);
-            for (int32_t gi = 0; gi < n_groups; ++gi) groups[gi].clear();
-            for (size_t i = 0; i < rq.size(); ++i)
-                if (rq[i].chain >= 0 && rq[i].chain < n_groups) groups[rq[i].chain].push_back(i);
-            thread_local std::vector<const WinReq *> g;
-            for (int32_t gi = 0; gi < n_groups; ++gi) {
-                const std::vector<size_t> &members = groups[gi];
-                if (members.size() < 2) continue;
-                g.clear();
-                for (size_t i : members) g.push_back(&rq[i]);
+            const bool chains_on = ctx->opt_incremental != 0 && est == 0;
+            // A chain's requests are consecutive (its base window first): walk the runs.
+            size_t i = 0;
+            while (i < rq.size()) {
+                size_t e = i + 1;
+                if (chains_on && rq[i].chain >= 0)
+                    while (e < rq.size() && rq[e].chain == rq[i].chain) ++e;
                 bool use = false;
-                if (ctx->opt_incremental == 2) use = true;
-                if (ctx->opt_incremental == 1) use = chain_cost(g, k_nb) < 0.5 * scratch_cost(g);
-                if (!use) continue;
-                ChainSpec sp;
-                sp.xs = ms[q]->xs;
-                sp.ys = ms[q]->ys;
-                for (size_t i : members) {
-                    sp.starts.push_back(rq[i].start);
-                    sp.sizes.push_back(rq[i].m);
-                    sp.out_idx.push_back(rq[i].base ? -1 : (int64_t)(rd.first[q] + i));
-                    in_chain[i] = 1;
+                if (e - i >= 2) {
+                    thread_local std::vector<const WinReq *> g;
+                    g.clear();
+                    for (size_t u = i; u < e; ++u) g.push_back(&rq[u]);
+                    if (ctx->opt_incremental == 2) use = true;
+                    if (ctx->opt_incremental == 1) use = chain_cost(g, k_nb) < 0.5 * scratch_cost(g);
                 }
-                chains.push_back(std::move(sp));
-            }
-            for (size_t i = 0; i < rq.size(); ++i) {
-                if (in_chain[i] || rq[i].base) continue;
-                batch.push_back(HostWindow{ms[q]->xs, ms[q]->ys, rq[i].start, rq[i].m});
-                where.push_back(rd.first[q] + i);
+                if (use) {
+                    ChainSpec sp;
+                    sp.xs = ms[q]->xs;
+                    sp.ys = ms[q]->ys;
+                    for (size_t u = i; u < e; ++u) {
+                        sp.starts.push_back(rq[u].start);
+                        sp.sizes.push_back(rq[u].m);
+                        sp.out_idx.push_back(rq[u].base ? -1 : (int64_t)(rd.first[q] + u));
+                    }
+                    chains.push_back(std::move(sp));
+                } else {
+                    for (size_t u = i; u < e; ++u) {
+                        if (rq[u].base) continue;
+                        batch.push_back(HostWindow{ms[q]->xs, ms[q]->ys, rq[u].start, rq[u].m});
+                        where.push_back(rd.first[q] + u);
+                    }
+                }
+                i = e;
             }
         }
         if (!chains.empty()) {
