@@ -356,6 +356,8 @@ def search_case(args):
     if args.speculation >= 0:
         api.isycos_set_option(ctx, api.OPT_SPECULATION, args.speculation)
     ids = [(api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)) for x, y in pairs]
+    # the MI path per window size, chosen on this GPU as in the default step
+    tune = api.isycos_autotune(ctx, PARAMS["k"])
     extra = {"td": [dict(mode=0)], "bu": [dict(mode=1)], "mix": [dict(mode=0), dict(mode=1)],
              "select": [dict(mode=2)], "chunked": [dict(mode=1, chunks=8)]}[args.search_case]
     qs = [(a, b, 0, args.length, dict(PARAMS, **e)) for e in extra for a, b in ids]
@@ -372,6 +374,7 @@ def search_case(args):
     k = args.steps
     line = {"search_case": args.search_case, "pairs": args.case_pairs, "length": args.length,
             "lanes": args.lanes, "speculation": args.speculation,
+            "sorted_buckets": tune["sorted_buckets"],
             "s_per_pass": round(dt, 4), "decided_windows": st["decided_windows"] // k,
             "gpu_windows": st["windows"] // k, "launches": st["launches"] // k,
             "kernel_ms": round(st["mi_kernel_ms"] / k, 2),

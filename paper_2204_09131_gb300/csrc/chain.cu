@@ -32,20 +32,21 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Stable insertion of (d, j) into the ascending list (candidates arrive in increasing j):
+// every position is computed from the old list at once, so the dependent depth is one compare
+// and two selects; with d >= the last entry nothing changes.
 template <int K1>
 __device__ __forceinline__ void insert_sorted(float (&bd)[K1], int (&bj)[K1], float d, int j) {
-    bd[K1 - 1] = d;
-    bj[K1 - 1] = j;
+    bool c[K1];
+#pragma unroll
+    for (int r = 0; r < K1; ++r) c[r] = bd[r] > d;
 #pragma unroll
     for (int r = K1 - 1; r > 0; --r) {
-        const bool sw = bd[r] < bd[r - 1];
-        const float a0 = bd[r - 1], a1 = bd[r];
-        const int b0 = bj[r - 1], b1 = bj[r];
-        bd[r - 1] = sw ? a1 : a0;
-        bd[r] = sw ? a0 : a1;
-        bj[r - 1] = sw ? b1 : b0;
-        bj[r] = sw ? b0 : b1;
+        bd[r] = c[r - 1] ? bd[r - 1] : (c[r] ? d : bd[r]);
+        bj[r] = c[r - 1] ? bj[r - 1] : (c[r] ? j : bj[r]);
     }
+    bd[0] = c[0] ? d : bd[0];
+    bj[0] = c[0] ? j : bj[0];
 }
 
 // Full neighbour search and counts for one point (time index tp) over the window

@@ -377,9 +377,33 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 const int jj = __float_as_int(c.z);
                 if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
             };
+            // four candidates u, u + dir, u + 2 dir, u + 3 dir: loads and distances first, then
+            // the insertions (the list is the same in any visiting order)
+            auto visit4 = [&](int u, int dir) {
+                float4 c[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[q] = rec[u + q * dir];
+                float d[4];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    d[q] = fmaxf(fabsf(xi - c[q].x), fabsf(yi - c[q].y));
+                    any |= d[q] <= bd[K1 - 1];
+                }
+                if (any) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jj = __float_as_int(c[q].z);
+                        if (d[q] < bd[K1 - 1] || (d[q] == bd[K1 - 1] && jj < bj[K1 - 1]))
+                            insert_lex<K1>(bd, bj, d[q], jj);
+                    }
+                }
+            };
             // the 64 points around the chunk (the point itself among them)
             const int a0 = max(0, c0 - 16), a1 = min(m, c0 + 48);
-            for (int u = a0; u < a1; ++u) visit(u);
+            int u = a0;
+            for (; u + 4 <= a1; u += 4) visit4(u, 1);
+            for (; u < a1; ++u) visit(u);
             // outward, while some lane's strip reaches the next point
             int L = a0 - 1, R = a1;
             for (;;) {
@@ -387,12 +411,22 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 const bool need_r = R < m && __any_sync(kFull, valid && fabsf(xi - rec[R].x) <= bd[K1 - 1]);
                 if (!need_l && !need_r) break;
                 if (need_l) {
-                    const int stop = max(L - 8, -1);
-                    for (; L > stop; --L) visit(L);
+                    if (L >= 7) {
+                        visit4(L, -1);
+                        visit4(L - 4, -1);
+                        L -= 8;
+                    } else {
+                        for (; L >= 0; --L) visit(L);
+                    }
                 }
                 if (need_r) {
-                    const int stop = min(R + 8, m);
-                    for (; R < stop; ++R) visit(R);
+                    if (R + 8 <= m) {
+                        visit4(R, 1);
+                        visit4(R + 4, 1);
+                        R += 8;
+                    } else {
+                        for (; R < m; ++R) visit(R);
+                    }
                 }
             }
             if (valid) {
