@@ -285,6 +285,81 @@ __device__ void bitonic_sort(T *k, int N) {   // N a power of two, called by all
         }
 }
 
+// The same network with the elements in registers: thread t of warp w holds the E elements
+// (w E + q) 32 + lane, q < E (N = NT E).  Steps with partner distance j < 32 pair lanes of one
+// warp (shuffles); 32 <= j < 32 E pair registers of one thread; only j >= 32 E goes through
+// shared memory with CTA barriers (15 of the 78 steps at N = 4096, E = 4).
+template <int NT, int E, typename T>
+__device__ void bitonic_sort_reg(T *k, int N) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = k[(w * E + q) * 32 + lane];
+    for (int k2 = 2; k2 <= N; k2 <<= 1) {
+        int j = k2 >> 1;
+        if (j >= 32 * E) {
+            __syncthreads();   // every thread has read the previous shared-memory state
+#pragma unroll
+            for (int q = 0; q < E; ++q) k[(w * E + q) * 32 + lane] = v[q];
+            __syncthreads();
+            for (; j >= 32 * E; j >>= 1) {
+                for (int i = threadIdx.x; i < N; i += NT) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const T a = k[i], b = k[ixj];
+                        if ((a > b) == ((i & k2) == 0)) {
+                            k[i] = b;
+                            k[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < E; ++q) v[q] = k[(w * E + q) * 32 + lane];
+        }
+        // (register indices stay compile-time: jq runs over the constants E / 2, ..., 1)
+#pragma unroll
+        for (int jq = E / 2; jq >= 1; jq >>= 1) {
+            if (jq * 32 > (k2 >> 1)) continue;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                if (q & jq) continue;
+                const int p = q | jq;
+                const bool up = ((((w * E + q) * 32 + lane) & k2) == 0);
+                const T a = v[q], b = v[p];
+                const bool sw = (a > b) == up;
+                v[q] = sw ? b : a;
+                v[p] = sw ? a : b;
+            }
+        }
+        for (j = min(16, k2 >> 1); j >= 1; j >>= 1) {
+            const bool lower = (lane & j) == 0;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const T a = v[q];
+                const T b = __shfl_xor_sync(kFull, a, j);
+                const bool up = ((((w * E + q) * 32 + lane) & k2) == 0);
+                v[q] = (lower == up) ? (b < a ? b : a) : (b > a ? b : a);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E; ++q) k[(w * E + q) * 32 + lane] = v[q];
+    __syncthreads();
+}
+
+// Sort N (a power of two) keys in shared or global memory with all NT threads: in registers
+// when N is 1, 2 or 4 times NT, else in memory throughout.
+template <int NT, typename T>
+__device__ void sort_keys(T *k, int N) {
+    if (N == NT) bitonic_sort_reg<NT, 1>(k, N);
+    else if (N == 2 * NT) bitonic_sort_reg<NT, 2>(k, N);
+    else if (N == 4 * NT) bitonic_sort_reg<NT, 4>(k, N);
+    else bitonic_sort<NT>(k, N);
+}
+
 // The same insertion under the lexicographic order of (d, j), for candidates that arrive
 // out of index order.
 template <int K1>
@@ -320,7 +395,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     for (int i = threadIdx.x; i < N; i += NT)
         keys[i] = i < m ? (((unsigned long long)fkey(s[i].x) << 32) | (unsigned)i) : ~0ull;
     __syncthreads();
-    bitonic_sort<NT>(keys, N);
+    sort_keys<NT>(keys, N);
     for (int t = threadIdx.x; t < m; t += NT) {
         const int j = (int)(keys[t] & 0xffffffffu);
         rec[t] = make_float4(s[j].x, s[j].y, __int_as_float(j), 0.0f);
@@ -329,7 +404,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     float *ys = reinterpret_cast<float *>(keys);   // the keys are no longer needed
     for (int i = threadIdx.x; i < N; i += NT) ys[i] = i < m ? s[i].y : kInf;
     __syncthreads();
-    bitonic_sort<NT>(ys, N);
+    sort_keys<NT>(ys, N);
 
     // Phase A: the neighbour lists, by outward scans.  A warp takes 32 consecutive points of
     // the x order (a chunk, from a shared counter).  Every lane first scans the 64 points of
