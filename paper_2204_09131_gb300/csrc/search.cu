@@ -74,6 +74,7 @@ public:
 
     bool want(std::vector<WinReq> &req) override {
         asked_.clear();
+        dest_.clear();
         next_chain_ = 0;
         for (;;) {
             if (finished_) return false;
@@ -100,7 +101,19 @@ public:
         }
     }
 
-    void give(const isycos_mi_out *res, size_t n) override { absorb(res, n); }
+    void give(const isycos_mi_out *res, size_t n) override {
+        for (size_t i = 0; i < n && i < asked_.size(); ++i) {
+            const Val v{score_of(res[i]), res[i].mi};
+            const Dest &d = dest_[i];
+            if (d.slot >= 0) {
+                Slot &q = slots_[(size_t)d.slot];
+                q.v[d.kind] = v;
+                q.have |= (uint8_t)(1u << d.kind);
+            } else {
+                cache_.put(key(asked_[i].start, asked_[i].m), v);
+            }
+        }
+    }
 
     void init() { s_w_ = prm.s_max; }
 
@@ -111,6 +124,20 @@ private:
         bool shifted;        // the window at t is the previous one moved by delta
         int run;             // consecutive noise detections
         bool done;
+        int64_t off;         // first score slot of the partition in this layer
+    };
+    // Scores of one layer, one slot per grid position a + i delta of a partition: the grid
+    // window (kind 0) and the noise test's sub-windows w_o = [t, t + s_w - delta - 1] (kind 1)
+    // and w_delta = [t + s_w - delta, t + s_w - 1] (kind 2).  The scans ask and read them in
+    // position order, so the slots are filled and read sequentially.  A window off the grid
+    // (delta not dividing a jump) goes to the hashed cache.
+    struct Slot {
+        Val v[3];
+        uint8_t have = 0;
+    };
+    struct Dest {
+        int64_t slot;        // -1: the hashed cache
+        int kind;
     };
 
     int64_t delta() const {
@@ -122,16 +149,41 @@ private:
         std::sort(found.begin(), found.end(),
                   [](const isycos_result_window &u, const isycos_result_window &v) { return u.t_s < v.t_s; });
         scans_.clear();
-        int64_t cur = t_begin;
+        const int64_t d = delta();
+        int64_t cur = t_begin, slots = 0;
         auto add = [&](int64_t a, int64_t b) {
-            if (b - a + 1 >= s_w_) scans_.push_back(Scan{a, b, a, false, 0, false});
+            if (b - a + 1 >= s_w_) {
+                scans_.push_back(Scan{a, b, a, false, 0, false, slots});
+                slots += (b - a) / d + 1;
+            }
         };
         for (const auto &w : found) {
             if (w.t_s > cur) add(cur, w.t_s - 1);
             cur = w.t_e + 1;
         }
         if (cur <= t_end - 1) add(cur, t_end - 1);
+        slots_.assign((size_t)slots, Slot{});
         layer_started_ = true;
+    }
+
+    // Slot of position t of scan sc, or -1 when t is off the partition's grid.
+    int64_t slot_of(const Scan &sc, int64_t t) const {
+        const int64_t d = delta(), r = t - sc.a;
+        return r % d == 0 ? sc.off + r / d : -1;
+    }
+    // Score of the window of `kind` at position t of scan sc (m points), if known.
+    bool score(const Scan &sc, int64_t t, int kind, int32_t m, Val *v) const {
+        const int64_t q = slot_of(sc, t);
+        if (q < 0) return lookup(kind == 2 ? t + s_w_ - delta() : t, m, v);
+        const Slot &z = slots_[(size_t)q];
+        if (!(z.have & (1u << kind))) return false;
+        *v = z.v[kind];
+        return true;
+    }
+    void ask(const Scan &sc, int64_t t, int kind, int32_t m, int32_t chain) {
+        const int64_t start = kind == 2 ? t + s_w_ - delta() : t;
+        asked_.push_back(WinReq{start, m, chain, false});
+        dest_.push_back(Dest{slot_of(sc, t), kind});
     }
 
     // Ask for the grid windows of a scan from position t to the partition's end; the grid
@@ -142,19 +194,19 @@ private:
         const int32_t chain = next_chain_++;
         for (int64_t t = sc.t; t + s_w_ - 1 <= sc.b; t += d) {
             Val v;
-            if (!lookup(t, (int32_t)s_w_, &v)) asked_.push_back(WinReq{t, (int32_t)s_w_, chain, false});
-            if (prm.pruning && shifted) ask_subs(t);
+            if (!score(sc, t, 0, (int32_t)s_w_, &v)) ask(sc, t, 0, (int32_t)s_w_, chain);
+            if (prm.pruning && shifted) ask_subs(sc, t);
             shifted = true;
         }
     }
 
-    void ask_subs(int64_t t) {
+    void ask_subs(const Scan &sc, int64_t t) {
         const int64_t d = delta();
         const int64_t mo = s_w_ - d;
         if (mo < prm.k + 1 || d < prm.k + 1) return;
         Val v;
-        if (!lookup(t, (int32_t)mo, &v)) asked_.push_back(WinReq{t, (int32_t)mo});
-        if (!lookup(t + mo, (int32_t)d, &v)) asked_.push_back(WinReq{t + mo, (int32_t)d});
+        if (!score(sc, t, 1, (int32_t)mo, &v)) ask(sc, t, 1, (int32_t)mo, -1);
+        if (!score(sc, t, 2, (int32_t)d, &v)) ask(sc, t, 2, (int32_t)d, -1);
     }
 
     // Run the sequential scan on cached scores until a score is missing or the scan ends.
@@ -166,7 +218,7 @@ private:
                 return;
             }
             Val w;
-            if (!lookup(sc.t, (int32_t)s_w_, &w)) {
+            if (!score(sc, sc.t, 0, (int32_t)s_w_, &w)) {
                 ask_grid(sc);
                 return;
             }
@@ -183,7 +235,7 @@ private:
                 const int64_t mo = s_w_ - d;
                 if (mo >= prm.k + 1 && d >= prm.k + 1) {
                     Val o, e;
-                    if (!lookup(sc.t, (int32_t)mo, &o) || !lookup(sc.t + mo, (int32_t)d, &e)) {
+                    if (!score(sc, sc.t, 1, (int32_t)mo, &o) || !score(sc, sc.t, 2, (int32_t)d, &e)) {
                         ask_grid(sc);
                         return;
                     }
@@ -217,6 +269,8 @@ private:
     bool layer_started_ = false;
     bool finished_ = false;
     std::vector<Scan> scans_;
+    std::vector<Slot> slots_;
+    std::vector<Dest> dest_;
 };
 
 // ---------------------------------------------------------------------------------------
