@@ -9,7 +9,9 @@ lanes, each lane merging its queries' window frontiers into persistent, size-buc
 launches.  The series stay resident in HBM (value); the e2e figure uploads them from pinned
 host memory and reads the found windows back inside the timed region.
 
-The JSON line follows the driver's contract; see the design doc for the roofline definition.
+One JSON line per run.  Its roofline counts 11 lane operations per ordered pair m (m - 1) of
+every evaluated window (brute-force-equivalent work) over the union of the MI kernel's launch
+intervals, against 152 SMs x 4 warp instructions per clock x 32 lanes at the sampled SM clock.
 """
 from __future__ import annotations
 

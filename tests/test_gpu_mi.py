@@ -2,8 +2,8 @@
 
 The bar: per-point integers (n_x, n_y, c) and the integer sums S_psi, S_log bit-exact; the
 binary64 scalars mi, h_w, nmi within 1e-12 (the path evaluates them in the same fixed order
-from the same exact sums, so they agree to the last bit in practice; the north-star
-tolerance is 1e-5).
+from the same exact sums, so they agree to the last bit in practice; the tolerance stated
+for these scalars is 1e-5).
 """
 import numpy as np
 import pytest
@@ -280,6 +280,36 @@ def test_sorted_path_equals_brute_force(ctx):
             assert got["s_psi"][0] == r["s_psi"] and got["mi"][0] == r["mi"]
         api.isycos_drop_series(ctx, xs)
         api.isycos_drop_series(ctx, ys)
+
+
+def test_sorted_path_every_sort_form_in_one_launch(ctx):
+    """One launch of 1024-thread CTAs (its largest sorted window has more than 1024 points)
+    holding sorted windows whose slot counts are below, equal to, twice and four times the
+    CTA's threads, and above 4096 points: the sort runs in memory, with one, two and four
+    keys per thread in registers, and in global scratch.  Per-point results equal the
+    brute-force path, on smooth, tied and constant data, for k = 1, 4 and 8."""
+    api = _api()
+    n = 30000
+    x, y, _ = synth.planted_pair(8, 5, n)
+    base = synth.normal(synth.seed_for(205, 0), n).astype(np.float32)
+    cases = [(x, y), (synth.quantize(x), synth.quantize(y)), (np.full(n, 1.5, np.float32), base)]
+    sizes = [300, 512, 513, 700, 1024, 1025, 1500, 2048, 2049, 3000, 4096, 5000, 257]
+    starts = [17 + 2100 * i for i in range(len(sizes))]
+    try:
+        for ci, (xx, yy) in enumerate(cases):
+            xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
+            w = api.windows_array(xs, ys, starts, sizes)
+            for k in (1, 4, 8):
+                res = {}
+                for opt in (1, 2):
+                    api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+                    res[opt] = api.isycos_mi_windows_points(ctx, w, k)
+                for a, b in zip(res[1], res[2]):
+                    assert np.array_equal(a, b), (ci, k)
+            api.isycos_drop_series(ctx, xs)
+            api.isycos_drop_series(ctx, ys)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
 
 
 def _check_points_est1(ctx, x, y, starts, sizes, k):
