@@ -338,6 +338,7 @@ public:
                 if (asked_.size() > before) {
                     for (int rr = r + 1; rr <= r_last; ++rr) ask_ring(rr, dropped_[0], dropped_[1], false);
                     speculate_next_climbs();
+                    speculate_ext_moves();
                 }
                 // (a ring whose scores are all cached has nothing to ask; if its decision
                 // still finds one missing, the next ask ignores the caches)
@@ -634,6 +635,37 @@ private:
             }
         }
     }
+    // Speculation within a climb, for the noise test (Sec. 6.2).  The test at a window needs
+    // the extension windows [t_s - r delta, t_s - 1] and [t_e + 1, t_e + r delta], r = 1 ..
+    // T_maxIdle + 1, which depend on the window's own ends: after each move the next decision
+    // would wait for them.  When a round goes to the GPU anyway, also ask those of the ends
+    // up to kExtMoves deltas away (positions asked before are remembered; the scores are
+    // cached and read only if the climb gets there).
+    static constexpr int kExtMoves = 8;
+    void speculate_ext_moves() {
+        if (!prm.pruning || prm.t_max_idle < 0) return;
+        if (ext_left_.size() > 4096) ext_left_.clear();
+        if (ext_right_.size() > 4096) ext_right_.clear();
+        const int64_t d = prm.delta_bu;
+        Val seen;
+        for (int a = -kExtMoves; a <= kExtMoves; ++a) {
+            const int64_t p = ws_ + a * d, q = we_ + a * d;
+            if (!ext_left_.find((uint64_t)p, &seen)) {
+                ext_left_.put((uint64_t)p, Val{0.0, 0.0});
+                for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
+                    const int64_t span = (int64_t)r * d;
+                    if (p - span >= t_begin && p - span > last_end_) spec_ext(p - span, p - 1);
+                }
+            }
+            if (!ext_right_.find((uint64_t)q, &seen)) {
+                ext_right_.put((uint64_t)q, Val{0.0, 0.0});
+                for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
+                    const int64_t span = (int64_t)r * d;
+                    if (q + 1 >= t_begin && q + 1 > last_end_ && q + span <= t_end - 1) spec_ext(q + 1, q + span);
+                }
+            }
+        }
+    }
     void spec_cell(int64_t a, int64_t b, int64_t ts, int64_t te) {
         if (grid_.known_or_asked(a, b, round_)) return;
         // never take a slot that holds a cell asked in this round
@@ -779,6 +811,8 @@ private:
     ExtCache ext_;
     uint32_t round_ = 0;
     FlatCache spec_starts_;   // climb starts whose windows were asked speculatively
+    FlatCache ext_left_;      // window starts whose left extension windows were asked ahead
+    FlatCache ext_right_;     // window ends whose right extension windows were asked ahead
     int32_t next_chain_ = 0;
 };
 
