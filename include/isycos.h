@@ -341,8 +341,8 @@ isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuning *out);
                                       psi(n_y + 1)> with strict counts in strips of half-width
                                       eps_i (searches take isycos_params.estimator)          */
 #define ISYCOS_OPT_SPECULATION 7   /* SYCOS_BU: climbs whose first windows are asked ahead,
-                                      assuming each ends where it starts; 0 .. 16 (default
-                                      12).  Changes the GPU work only, never the results     */
+                                      assuming each ends where it starts; 0 .. 64 (default
+                                      24).  Changes the GPU work only, never the results     */
 isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
 
 /* Window MI that allocates nothing.  The paper has no counterpart: this entry point

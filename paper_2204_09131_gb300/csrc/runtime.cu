@@ -876,7 +876,7 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) 
             ctx->opt_estimator = (int)value;
             return ISYCOS_OK;
         case ISYCOS_OPT_SPECULATION:
-            if (value < 0 || value > 16) break;
+            if (value < 0 || value > 64) break;
             ctx->opt_spec_climbs = (int)value;
             return ISYCOS_OK;
         default:

@@ -117,7 +117,7 @@ struct isycos_ctx {
     int opt_kernel = 0;
     int opt_incremental = 1;
     int opt_estimator = 0;   // estimator of the direct window-MI entry points
-    int opt_spec_climbs = 12; // SYCOS_BU climbs speculated ahead
+    int opt_spec_climbs = 24; // SYCOS_BU climbs speculated ahead
     // sorted-path buckets chosen by isycos_autotune, per k (0: not tuned, use the default)
     uint32_t tuned_sort_mask[ISYCOS_MAX_K + 1] = {0};
     bool tuned[ISYCOS_MAX_K + 1] = {false};

@@ -316,6 +316,7 @@ public:
                 phase_ = kWaitStart;
                 if (asked_.empty()) continue;
                 speculate_next_climbs();
+                speculate_ext_moves();
                 break;
             }
             if (phase_ == kWaitStart) {
@@ -380,6 +381,7 @@ public:
         L_.assign(prm.h, 0.0);
         cand_.reserve((size_t)8 * (prm.t_max_idle + 1));
         ring_ext_.assign((size_t)2 * (prm.t_max_idle + 2), RingExt{});
+        ext_.init(prm.delta_bu, prm.t_max_idle + 1);
         // the cells one round asks span T_maxIdle + 1 cells around the window and the windows
         // of the climbs asked ahead, s_min / delta cells apart: the direct-mapped array must
         // be wider than that span so that they do not evict one another
@@ -473,19 +475,30 @@ private:
             c.kb = b;
         }
     };
-    // Scores of noise-test extension windows (start, size): a small direct-mapped cache.
+    // Scores of the noise test's extension windows.  The left one of a window starting at p
+    // is [p - r delta, p - 1], the right one of a window ending at q is [q + 1, q + r delta]
+    // (r = 1 .. T_maxIdle + 1); one window can be both.  Slot: start / delta mod P and r, so
+    // that the windows near the search cursor never evict one another (the window itself is
+    // kept to tell it from the windows P deltas away that share the slot).
     struct ExtCache {
-        static constexpr int N = 4096;
+        static constexpr int P = 2048;
+        int R = 1;
+        int64_t d = 1;
         struct E {
             int64_t s = -1, m = 0;
             uint32_t asked = 0;
             bool have = false;
             Val v{0.0, 0.0};
         };
-        std::vector<E> e = std::vector<E>(N);
-        static size_t slot(int64_t s, int64_t m) {
-            uint64_t k = ((uint64_t)s * 0x9E3779B97F4A7C15ULL) ^ ((uint64_t)m * 0xC2B2AE3D27D4EB4FULL);
-            return (size_t)(k >> 52) & (N - 1);
+        std::vector<E> e;
+        void init(int64_t delta, int rmax) {
+            d = std::max<int64_t>(1, delta);
+            R = std::max(1, rmax);
+            e.assign((size_t)P * R, E{});
+        }
+        size_t slot(int64_t s, int64_t m) const {
+            const int64_t r = std::max<int64_t>(1, m / d);
+            return (size_t)((std::max<int64_t>(0, s) / d) & (P - 1)) * (size_t)R + (size_t)((r - 1) % R);
         }
         bool get(int64_t s, int64_t m, Val *v) const {
             const E &x = e[slot(s, m)];
@@ -629,8 +642,8 @@ private:
                     }
                 if (prm.pruning && (int64_t)r * d >= prm.k + 1) {
                     const int64_t span = (int64_t)r * d;
-                    if (cs - span >= t_begin && cs - span > last_end_) spec_ext(cs - span, cs - 1);
-                    if (ce + span <= t_end - 1) spec_ext(ce + 1, ce + span);
+                    if (cs - span >= t_begin && cs - span > last_end_) spec_ext(cs - span, cs - 1, 0);
+                    if (ce + span <= t_end - 1) spec_ext(ce + 1, ce + span, 1);
                 }
             }
         }
@@ -654,14 +667,14 @@ private:
                 ext_left_.put((uint64_t)p, Val{0.0, 0.0});
                 for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
                     const int64_t span = (int64_t)r * d;
-                    if (p - span >= t_begin && p - span > last_end_) spec_ext(p - span, p - 1);
+                    if (p - span >= t_begin && p - span > last_end_) spec_ext(p - span, p - 1, 0);
                 }
             }
             if (!ext_right_.find((uint64_t)q, &seen)) {
                 ext_right_.put((uint64_t)q, Val{0.0, 0.0});
                 for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
                     const int64_t span = (int64_t)r * d;
-                    if (q + 1 >= t_begin && q + 1 > last_end_ && q + span <= t_end - 1) spec_ext(q + 1, q + span);
+                    if (q + 1 >= t_begin && q + 1 > last_end_ && q + span <= t_end - 1) spec_ext(q + 1, q + span, 1);
                 }
             }
         }
@@ -672,13 +685,13 @@ private:
         if (grid_.taken(a, b, round_)) return;
         ask_cell(a, b, ts, te, kDestCell, -1, -1);
     }
-    void spec_ext(int64_t ts, int64_t te) {
+    void spec_ext(int64_t ts, int64_t te, int side) {
         const int64_t m = te - ts + 1;
         if (m < prm.k + 1) return;
         Val v;
         if (ext_.get(ts, m, &v)) return;
         if (!ext_.mark(ts, m, round_)) return;
-        ask_ext(ts, te, -1, 0);
+        ask_ext(ts, te, -1, side);
     }
 
     // Rings asked per round for the current window size (speculation depth).

@@ -376,7 +376,7 @@ def test_speculation_depth_changes_work_not_results(ctx):
     ref, n = O.search_bu(x, y, **okw)
     launches = {}
     try:
-        for depth in (0, 1, 3, 8, 12, 16):
+        for depth in (0, 1, 3, 8, 16, 24, 64):
             api.isycos_set_option(ctx, api.OPT_SPECULATION, depth)
             api.isycos_reset_stats(ctx)
             got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
@@ -385,7 +385,7 @@ def test_speculation_depth_changes_work_not_results(ctx):
             assert st["decided_windows"] == n
             launches[depth] = st["launches"]
     finally:
-        api.isycos_set_option(ctx, api.OPT_SPECULATION, 12)   # the default
+        api.isycos_set_option(ctx, api.OPT_SPECULATION, 24)   # the default
     assert launches[3] < launches[0]
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
