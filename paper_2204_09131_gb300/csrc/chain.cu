@@ -307,7 +307,13 @@ isycos_status engine_eval_chains(isycos_ctx *ctx, Lane &L, const ChainSpec *spec
     // Long chains are cut into segments so that about two segments per SM run at once;
     // each segment starts from scratch, so a segment holds at least 16 windows.
     int64_t total_steps = 0;
-    for (size_t c = 0; c < n_specs; ++c) total_steps += (int64_t)specs[c].starts.size();
+    for (size_t c = 0; c < n_specs; ++c) {
+        total_steps += (int64_t)specs[c].starts.size();
+        for (size_t i = 0; i < specs[c].starts.size(); ++i)
+            if (!window_in_series(ctx, specs[c].xs, specs[c].ys, specs[c].starts[i], specs[c].sizes[i], k))
+                return fail(ctx, ISYCOS_E_INVAL, "chain window [%lld, +%d] is outside its series",
+                            (long long)specs[c].starts[i], specs[c].sizes[i]);
+    }
     const int64_t seg_len = std::max<int64_t>(16, (total_steps + 2 * ctx->n_sm - 1) / (2 * ctx->n_sm));
     for (size_t c = 0; c < n_specs; ++c) {
         const ChainSpec &sp = specs[c];

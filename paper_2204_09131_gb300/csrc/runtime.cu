@@ -163,6 +163,12 @@ static isycos_status launch_grid(isycos_ctx *ctx, int k, int nt, size_t smem, in
     return ISYCOS_OK;
 }
 
+bool window_in_series(const isycos_ctx *ctx, int32_t xs, int32_t ys, int64_t start, int32_t m, int k) {
+    const int32_t ns = (int32_t)ctx->series_len.size();
+    if (xs < 0 || xs >= ns || ys < 0 || ys >= ns || m < k + 1 || m > kMaxM || start < 0) return false;
+    return start + m <= std::min(ctx->series_len[(size_t)xs], ctx->series_len[(size_t)ys]);
+}
+
 isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                             int est, int32_t *nx, int32_t *ny, int32_t *c, cudaStream_t st) {
     L.open.open = false;
@@ -175,6 +181,10 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     std::vector<int32_t> &slot = L.h_slot;
     slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
+        // every window must lie inside its resident series: the kernel reads it unchecked
+        if (!window_in_series(ctx, w[i].xs, w[i].ys, w[i].start, w[i].m, k))
+            return fail(ctx, ISYCOS_E_INVAL, "window %lld ([%lld, +%d] of series %d, %d) is outside its series",
+                        (long long)i, (long long)w[i].start, w[i].m, w[i].xs, w[i].ys);
         max_m = std::max(max_m, w[i].m);
         if ((smask >> size_bucket(w[i].m)) & 1u) {
             if (w[i].m <= kSortMax) max_sorted = std::max(max_sorted, w[i].m);

@@ -149,6 +149,9 @@ isycos_status engine_eval(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t
 // The same in two halves: engine_launch stages and launches (asynchronous on st), and
 // engine_collect waits for that launch and writes the results.  One launch per lane may be
 // open at a time.
+// The window [start, start + m - 1] of series xs and ys lies inside both series (and m is a
+// valid window size for k).  The engines check every window they are given with it.
+bool window_in_series(const isycos_ctx *ctx, int32_t xs, int32_t ys, int64_t start, int32_t m, int k);
 isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64_t n, int k,
                             int est, int32_t *nx, int32_t *ny, int32_t *c, cudaStream_t st);
 isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out);

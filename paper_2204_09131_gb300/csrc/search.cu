@@ -667,7 +667,7 @@ private:
                 ext_left_.put((uint64_t)p, Val{0.0, 0.0});
                 for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
                     const int64_t span = (int64_t)r * d;
-                    if (p - span >= t_begin && p - span > last_end_) spec_ext(p - span, p - 1, 0);
+                    if (p - span >= t_begin && p - span > last_end_ && p <= t_end) spec_ext(p - span, p - 1, 0);
                 }
             }
             if (!ext_right_.find((uint64_t)q, &seen)) {
@@ -680,6 +680,7 @@ private:
         }
     }
     void spec_cell(int64_t a, int64_t b, int64_t ts, int64_t te) {
+        if (ts < t_begin || te > t_end - 1) return;   // inside the range only
         if (grid_.known_or_asked(a, b, round_)) return;
         // never take a slot that holds a cell asked in this round
         if (grid_.taken(a, b, round_)) return;
@@ -687,7 +688,7 @@ private:
     }
     void spec_ext(int64_t ts, int64_t te, int side) {
         const int64_t m = te - ts + 1;
-        if (m < prm.k + 1) return;
+        if (m < prm.k + 1 || ts < t_begin || te > t_end - 1) return;   // inside the range only
         Val v;
         if (ext_.get(ts, m, &v)) return;
         if (!ext_.mark(ts, m, round_)) return;

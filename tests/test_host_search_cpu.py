@@ -1,0 +1,160 @@
+"""The library's search machines (SYCOS_TD, SYCOS_BU, Alg. 3 selection, Alg. 4 chunks) run
+on the host with window scores from the CPU oracle, against the oracle's own searches (CPU).
+
+`tests/host_search/host_search_main.cu` links the library's search logic (`csrc/search.cu`)
+with a stand-in engine that scores each window of a round with the oracle's estimator, so
+the decisions, the speculation and caching of the machines and the batching of a round are
+checked without a GPU: the found windows must be the oracle's, bit for bit, and the number
+of window scores the decisions read must equal the oracle's evaluation count.  The MI
+kernels are covered by the GPU tests.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2204_09131_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "host_search", "host_search_main.cu")
+BUILD = os.path.join(HERE, "host_search", "_build")
+EXE = os.path.join(BUILD, "host_search")
+
+
+@pytest.fixture(scope="module")
+def driver():
+    from paper_2204_09131_gb300 import build as B
+    try:
+        nvcc = B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    os.makedirs(BUILD, exist_ok=True)
+    obj = os.path.join(BUILD, "oracle.o")
+    subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-c",
+                    os.path.join(ROOT, "oracle", "isycos_oracle.c"), "-o", obj], check=True)
+    subprocess.run([nvcc, *B.ARCH, "-O2", "-std=c++17", "--expt-relaxed-constexpr",
+                    "-I" + B.INCLUDE, "-I" + B.CSRC, SRC, os.path.join(B.CSRC, "search.cu"), obj,
+                    "-o", EXE, "-lm"], check=True, capture_output=True)
+    return EXE
+
+
+def _series_file(tmp_path, pairs):
+    n = len(pairs[0][0])
+    path = os.path.join(str(tmp_path), "series.bin")
+    with open(path, "wb") as f:
+        np.array([len(pairs)], np.int32).tofile(f)
+        np.array([n], np.int64).tofile(f)
+        for x, y in pairs:
+            np.asarray(x, np.float32).tofile(f)
+            np.asarray(y, np.float32).tofile(f)
+    return path
+
+
+def _run(exe, path, **kw):
+    args = [exe, path] + ["%s=%s" % (k, v) for k, v in kw.items()]
+    out = subprocess.run(args, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    res, cur = [], None
+    for line in out.stdout.splitlines():
+        f = line.split()
+        if f[0] == "M":
+            cur = {"decided": int(f[3]), "found": []}
+            res.append(cur)
+        elif f[0] == "W":
+            cur["found"].append((int(f[1]), int(f[2]), float(f[3]), float(f[4])))
+    return res
+
+
+def _same(got, ref, n_ref):
+    assert [(a, b) for a, b, _, _ in got["found"]] == [(a, b) for a, b, _, _ in ref]
+    for (_, _, s, m), (_, _, rs, rm) in zip(got["found"], ref):
+        assert s == rs and m == rm
+    assert got["decided"] == n_ref
+
+
+@pytest.fixture(scope="module")
+def pairs():
+    x0, y0 = synth.planted_small_pair()
+    x1, y1, _ = synth.planted_pair(6, 3, len(x0))
+    return [(x0, y0), (x1, y1)]
+
+
+ORC_KEYS = ("k", "score_kind", "sigma", "tau", "s_min", "s_max", "delta_td", "delta_bu", "h",
+            "t_max_idle", "p", "pruning", "max_steps", "seed")
+
+CASES = [
+    # SYCOS_TD: pruning off / on, raw-MI scores, an explicit step that leaves the grid
+    dict(mode=0, pruning=0),
+    dict(mode=0, pruning=1),
+    dict(mode=0, pruning=1, score_kind=1, sigma=0.5, tau=0.1),
+    dict(mode=0, pruning=1, delta_td=7),
+    # SYCOS_BU: pruning off / on, seeds, idle limits, a step that does not divide s_min
+    dict(mode=1, pruning=0, seed=3),
+    dict(mode=1, pruning=1, seed=31),
+    dict(mode=1, pruning=1, score_kind=1, sigma=0.5, tau=0.1, seed=5),
+    dict(mode=1, pruning=1, t_max_idle=1, seed=7),
+    dict(mode=1, pruning=1, t_max_idle=5, h=3, seed=8),
+    dict(mode=1, pruning=1, delta_bu=5, seed=9),
+    # the second estimator's counterpart (Kraskov's first)
+    dict(mode=0, pruning=1, estimator=1),
+    dict(mode=1, pruning=1, estimator=1, seed=11),
+]
+
+
+@pytest.mark.parametrize("kw", CASES)
+def test_machines_match_oracle(driver, tmp_path, pairs, kw):
+    path = _series_file(tmp_path, pairs)
+    got = _run(driver, path, s_max=256, **kw)
+    okw = {k: v for k, v in kw.items() if k in ORC_KEYS}
+    for (x, y), g in zip(pairs, got):
+        ref, n = (O.search_td if kw["mode"] == 0 else O.search_bu)(
+            x, y, s_max=256, estimator=kw.get("estimator", 0), **okw)
+        _same(g, ref, n)
+
+
+@pytest.mark.parametrize("spec,incremental", [(0, 1), (1, 1), (24, 0), (64, 2)])
+def test_bu_speculation_and_chains_change_work_not_results(driver, tmp_path, pairs, spec,
+                                                            incremental):
+    """Climbs asked ahead, extension windows asked ahead and incremental chains change the
+    rounds, never the decisions."""
+    path = _series_file(tmp_path, pairs)
+    kw = dict(mode=1, pruning=1, seed=31)
+    got = _run(driver, path, s_max=256, spec=spec, incremental=incremental, **kw)
+    okw = {k: v for k, v in kw.items() if k != "mode"}
+    for (x, y), g in zip(pairs, got):
+        ref, n = O.search_bu(x, y, s_max=256, **okw)
+        _same(g, ref, n)
+
+
+def test_sub_range(driver, tmp_path, pairs):
+    path = _series_file(tmp_path, pairs)
+    for mode in (0, 1):
+        got = _run(driver, path, s_max=128, mode=mode, pruning=1, t_begin=300, t_end=1700)
+        for (x, y), g in zip(pairs, got):
+            ref, n = (O.search_td if mode == 0 else O.search_bu)(
+                x, y, t_begin=300, t_end=1700, s_max=128, pruning=1)
+            _same(g, ref, n)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chunked_matches_oracle(driver, tmp_path, pairs, mode):
+    """Algorithm 4: three overlapping chunks searched independently."""
+    path = _series_file(tmp_path, pairs)
+    got = _run(driver, path, s_max=128, mode=mode, pruning=1, chunks=3)
+    for (x, y), g in zip(pairs, got):
+        ref, n = O.search_chunked(x, y, mode=mode, chunks=3, s_max=128, pruning=1)
+        _same(g, ref, n)
+
+
+def test_selection_matches_oracle(driver, tmp_path, pairs):
+    """Algorithm 3: sampled partitions searched with both algorithms, then the choice."""
+    path = _series_file(tmp_path, pairs)
+    got = _run(driver, path, s_max=128, mode=2, pruning=1, sel_partitions=8, sel_samples=3)
+    for (x, y), g in zip(pairs, got):
+        ref, n, _, _ = O.search_auto(x, y, partitions=8, samples=3, s_max=128, pruning=1)
+        _same(g, ref, n)
