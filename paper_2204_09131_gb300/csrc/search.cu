@@ -493,7 +493,7 @@ private:
         std::vector<E> e;
         void init(int64_t delta, int rmax) {
             d = std::max<int64_t>(1, delta);
-            R = std::max(1, rmax);
+            R = std::max(1, std::min(rmax, 8));   // larger r share slots (r mod 8)
             e.assign((size_t)P * R, E{});
         }
         size_t slot(int64_t s, int64_t m) const {

@@ -99,6 +99,7 @@ CASES = [
     dict(mode=1, pruning=1, score_kind=1, sigma=0.5, tau=0.1, seed=5),
     dict(mode=1, pruning=1, t_max_idle=1, seed=7),
     dict(mode=1, pruning=1, t_max_idle=5, h=3, seed=8),
+    dict(mode=1, pruning=1, t_max_idle=10, seed=12),   # rings beyond 8 share cache slots
     dict(mode=1, pruning=1, delta_bu=5, seed=9),
     # the second estimator's counterpart (Kraskov's first)
     dict(mode=0, pruning=1, estimator=1),
