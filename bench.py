@@ -224,6 +224,8 @@ def reference_arm(args):
     if rank != 0:
         return
     pairs = make_pairs(0, 1, args.length)
+    for _ in range(args.warmup):   # untimed, like the other arm's warm-up steps
+        cpu_baseline(pairs)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
