@@ -276,6 +276,19 @@ private:
 // ---------------------------------------------------------------------------------------
 // SYCOS_BU
 // ---------------------------------------------------------------------------------------
+// Division by a lattice step that is usually a power of two (delta = s_min / 4): a shift
+// when it is one (the quotients taken here are exact multiples, or non-negative).
+struct StepDiv {
+    int64_t d = 1;
+    int sh = 0;   // log2(d) when d is a power of two, else -1
+    void set(int64_t delta) {
+        d = std::max<int64_t>(1, delta);
+        sh = (d & (d - 1)) == 0 ? __builtin_ctzll((unsigned long long)d) : -1;
+    }
+    int64_t div(int64_t x) const { return sh >= 0 ? (x >> sh) : x / d; }
+    bool divides(int64_t x) const { return sh >= 0 ? (x & (d - 1)) == 0 : x % d == 0; }
+};
+
 inline uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
     uint64_t z = seed + n * 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -410,6 +423,7 @@ private:
         };
         int G = 64, lg = 6;
         int64_t bs = 0, be = 0, d = 1;
+        StepDiv dv;
         uint32_t gen = 1;
         bool valid = false;
         std::vector<Slot> cell;
@@ -425,18 +439,20 @@ private:
             cell.assign((size_t)G * G, Slot{});
         }
         bool on_lattice(int64_t ws, int64_t we, int64_t delta) const {
-            return valid && delta == d && (ws - bs) % d == 0 && (we - be) % d == 0;
+            return valid && delta == d && dv.divides(ws - bs) && dv.divides(we - be);
         }
         void reset(int64_t s, int64_t e, int64_t delta) {
             bs = s;
             be = e;
             d = delta;
+            dv.set(delta);
             ++gen;
             valid = true;
         }
+        // (ws, we) on the lattice: the quotients are exact
         void centre(int64_t ws, int64_t we, int64_t *a, int64_t *b) const {
-            *a = (ws - bs) / d;
-            *b = (we - be) / d;
+            *a = dv.div(ws - bs);
+            *b = dv.div(we - be);
         }
         size_t slot(int64_t a, int64_t b) const {
             return ((size_t)(a & (G - 1)) << lg) | (size_t)(b & (G - 1));
@@ -482,8 +498,8 @@ private:
     // kept to tell it from the windows P deltas away that share the slot).
     struct ExtCache {
         static constexpr int P = 2048;
-        int R = 1;
-        int64_t d = 1;
+        int R = 1, rmask = 0;   // rmask = R - 1 when R is a power of two, else -1
+        StepDiv dv;
         struct E {
             int64_t s = -1, m = 0;
             uint32_t asked = 0;
@@ -492,13 +508,15 @@ private:
         };
         std::vector<E> e;
         void init(int64_t delta, int rmax) {
-            d = std::max<int64_t>(1, delta);
+            dv.set(delta);
             R = std::max(1, std::min(rmax, 8));   // larger r share slots (r mod 8)
+            rmask = (R & (R - 1)) == 0 ? R - 1 : -1;
             e.assign((size_t)P * R, E{});
         }
         size_t slot(int64_t s, int64_t m) const {
-            const int64_t r = std::max<int64_t>(1, m / d);
-            return (size_t)((std::max<int64_t>(0, s) / d) & (P - 1)) * (size_t)R + (size_t)((r - 1) % R);
+            const int64_t r1 = std::max<int64_t>(1, dv.div(m)) - 1;
+            const int64_t rq = rmask >= 0 ? (r1 & rmask) : r1 % R;
+            return (size_t)(dv.div(std::max<int64_t>(0, s)) & (P - 1)) * (size_t)R + (size_t)rq;
         }
         bool get(int64_t s, int64_t m, Val *v) const {
             const E &x = e[slot(s, m)];
