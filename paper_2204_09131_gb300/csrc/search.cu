@@ -381,8 +381,9 @@ public:
             } else if (d.kind == kDestExt) {
                 ext_.put(d.a, d.b, v);
                 // the extension windows of the rings asked for the next decisions are also
-                // kept by ring and side: the direct-mapped cache may lose one of them to
-                // another window of the same round
+                // kept by ring and side: the slotted cache may still lose one of them to
+                // another window of the same round (P deltas away, or a ring beyond the
+                // eighth sharing its slot)
                 if (d.r >= 0) ring_ext_[(size_t)(2 * d.r + d.side)] = RingExt{d.a, d.b, v};
             }
         }
