@@ -551,6 +551,26 @@ const char *isycos_last_error(const isycos_ctx *ctx) {
     return ctx->err.c_str();
 }
 
+// Index of the first value of d[0..n) that is not finite (exponent bits all ones: an
+// infinity or a NaN), or -1.  Blocks are tested without a branch per value, so that the
+// scan vectorises; only a block that holds a bad value is searched again for its index.
+static int64_t first_nonfinite(const float *d, int64_t n) {
+    constexpr int64_t kBlock = 4096;
+    for (int64_t s = 0; s < n; s += kBlock) {
+        const int64_t e = std::min(n, s + kBlock);
+        uint32_t bad = 0;
+        for (int64_t i = s; i < e; ++i) {
+            uint32_t u;
+            memcpy(&u, d + i, 4);
+            bad |= (u & 0x7f800000u) == 0x7f800000u;
+        }
+        if (bad)
+            for (int64_t i = s; i < e; ++i)
+                if (!isfinite(d[i])) return i;
+    }
+    return -1;
+}
+
 isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, int32_t on_device,
                                 int32_t *series_id) {
     if (!ctx) return ISYCOS_E_INVAL;
@@ -559,9 +579,8 @@ isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, i
     cudaSetDevice(ctx->device);
     const size_t bytes = sizeof(float) * (size_t)n;
     if (!on_device) {
-        for (int64_t i = 0; i < n; ++i)
-            if (!isfinite(data[i]))
-                return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld is not finite", (long long)i);
+        const int64_t i = first_nonfinite(data, n);
+        if (i >= 0) return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld is not finite", (long long)i);
     }
     if (ctx->used.load() + bytes > ctx->budget)
         return fail(ctx, ISYCOS_E_NOMEM, "put_series: device budget exceeded");
