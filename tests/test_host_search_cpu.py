@@ -159,3 +159,21 @@ def test_selection_matches_oracle(driver, tmp_path, pairs):
     for (x, y), g in zip(pairs, got):
         ref, n, _, _ = O.search_auto(x, y, partitions=8, samples=3, s_max=128, pruning=1)
         _same(g, ref, n)
+
+
+def test_launch_layout_invariants():
+    """The launch layout shared by the host runtime and the batched MI kernel (size buckets,
+    warps per item, bucket tables, grid size, shared-memory sizes) satisfies its invariants
+    (`tests/host_search/layout_main.cu`)."""
+    from paper_2204_09131_gb300 import build as B
+    try:
+        nvcc = B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    os.makedirs(BUILD, exist_ok=True)
+    exe = os.path.join(BUILD, "layout")
+    subprocess.run([nvcc, *B.ARCH, "-O2", "-std=c++17", "--expt-relaxed-constexpr",
+                    "-I" + B.INCLUDE, "-I" + B.CSRC, os.path.join(HERE, "host_search", "layout_main.cu"),
+                    "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout[-2000:]
