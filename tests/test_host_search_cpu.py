@@ -177,3 +177,30 @@ def test_launch_layout_invariants():
                     "-o", exe], check=True, capture_output=True)
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout[-2000:]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_configurations(driver, tmp_path, pairs, seed):
+    """Seeded random parameter sets and sub-ranges (k, window sizes, steps, idle limits,
+    noise thresholds): every window a machine asks for lies inside the range (the stand-in
+    engine rejects any other) and the decisions are the oracle's."""
+    rng = np.random.default_rng(1000 + seed)
+    k = int(rng.choice([2, 3, 4, 6]))
+    s_min = int(rng.choice([16, 24, 32, 40]))
+    s_max = int(rng.choice([s_min * 2, s_min * 4, 192, 256]))
+    s_max = max(s_max, s_min)
+    n = len(pairs[0][0])
+    t_begin = int(rng.integers(0, 400))
+    t_end = int(rng.integers(n - 400, n + 1))
+    kw = dict(k=k, s_min=s_min, s_max=s_max, pruning=int(rng.integers(0, 2)),
+              delta_bu=int(rng.choice([0, 3, 4, 7])), delta_td=int(rng.choice([0, 0, 5, 9])),
+              t_max_idle=int(rng.choice([1, 2, 3, 6])), h=int(rng.choice([4, 8, 12])),
+              sigma=float(rng.choice([0.15, 0.2, 0.3])), seed=int(rng.integers(0, 1 << 30)))
+    path = _series_file(tmp_path, pairs)
+    for mode in (0, 1):
+        got = _run(driver, path, mode=mode, t_begin=t_begin, t_end=t_end,
+                   spec=int(rng.choice([0, 5, 24])), **kw)
+        for (x, y), g in zip(pairs, got):
+            ref, n_ref = (O.search_td if mode == 0 else O.search_bu)(
+                x, y, t_begin=t_begin, t_end=t_end, **kw)
+            _same(g, ref, n_ref)
