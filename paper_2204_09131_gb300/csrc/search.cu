@@ -289,6 +289,21 @@ struct StepDiv {
     bool divides(int64_t x) const { return sh >= 0 ? (x & (d - 1)) == 0 : x % d == 0; }
 };
 
+// A set of positions near a moving cursor: direct mapped over position / step (exact
+// positions kept), so that nothing needs clearing as the cursor advances; positions
+// kSlots steps apart share a slot (the later one wins: a lost position is merely
+// speculated again).
+struct PosSet {
+    static constexpr int kSlots = 1024;
+    StepDiv dv;
+    std::vector<int64_t> key = std::vector<int64_t>(kSlots, INT64_MIN);
+    void init(int64_t step) { dv.set(step); }
+    void clear() { std::fill(key.begin(), key.end(), INT64_MIN); }
+    size_t slot(int64_t p) const { return (size_t)(dv.div(std::max<int64_t>(0, p)) & (kSlots - 1)); }
+    bool has(int64_t p) const { return key[slot(p)] == p; }
+    void add(int64_t p) { key[slot(p)] = p; }
+};
+
 inline uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
     uint64_t z = seed + n * 0x9E3779B97F4A7C15ULL;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -318,7 +333,6 @@ public:
                     grid_.reset(ws_, we_, prm.delta_bu);
                     spec_starts_.clear();
                 }
-                if (spec_starts_.size() > 256) spec_starts_.clear();   // starts behind the cursor
                 // a climb always evaluates ring N_1 of its first window next: ask it now
                 int64_t ac, bc;
                 grid_.centre(ws_, we_, &ac, &bc);
@@ -396,6 +410,9 @@ public:
         cand_.reserve((size_t)8 * (prm.t_max_idle + 1));
         ring_ext_.assign((size_t)2 * (prm.t_max_idle + 2), RingExt{});
         ext_.init(prm.delta_bu, prm.t_max_idle + 1);
+        spec_starts_.init(prm.delta_bu);
+        ext_left_.init(prm.delta_bu);
+        ext_right_.init(prm.delta_bu);
         // the cells one round asks span T_maxIdle + 1 cells around the window and the windows
         // of the climbs asked ahead, s_min / delta cells apart: the direct-mapped array must
         // be wider than that span so that they do not evict one another
@@ -639,14 +656,13 @@ private:
             if (c + sm > t_end) return;
             const int64_t cs = c, ce = c + sm - 1;
             if (!grid_.on_lattice(cs, ce, d)) return;   // cached only on the grid's lattice
-            Val seen;
-            if (spec_starts_.find((uint64_t)c, &seen)) continue;   // asked in an earlier round
-            spec_starts_.put((uint64_t)c, Val{0.0, 0.0});
+            if (spec_starts_.has(c)) continue;   // asked in an earlier round
+            spec_starts_.add(c);
             // When the start one delta earlier was asked ahead too, its square of cells
             // (offsets up to `depth` around it) holds every cell of this one but those at
             // offset +depth in a or b: ask only those (a cell the cache has lost since is asked
             // again when a decision needs it).
-            const bool near = spec_starts_.find((uint64_t)(c - d), &seen);
+            const bool near = spec_starts_.has(c - d);
             int64_t ac, bc;
             grid_.centre(cs, ce, &ac, &bc);
             if (!near) spec_cell(ac, bc, cs, ce);
@@ -676,21 +692,18 @@ private:
     static constexpr int kExtMoves = 8;
     void speculate_ext_moves() {
         if (!prm.pruning || prm.t_max_idle < 0) return;
-        if (ext_left_.size() > 4096) ext_left_.clear();
-        if (ext_right_.size() > 4096) ext_right_.clear();
         const int64_t d = prm.delta_bu;
-        Val seen;
         for (int a = -kExtMoves; a <= kExtMoves; ++a) {
             const int64_t p = ws_ + a * d, q = we_ + a * d;
-            if (!ext_left_.find((uint64_t)p, &seen)) {
-                ext_left_.put((uint64_t)p, Val{0.0, 0.0});
+            if (!ext_left_.has(p)) {
+                ext_left_.add(p);
                 for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
                     const int64_t span = (int64_t)r * d;
                     if (p - span >= t_begin && p - span > last_end_ && p <= t_end) spec_ext(p - span, p - 1, 0);
                 }
             }
-            if (!ext_right_.find((uint64_t)q, &seen)) {
-                ext_right_.put((uint64_t)q, Val{0.0, 0.0});
+            if (!ext_right_.has(q)) {
+                ext_right_.add(q);
                 for (int r = 1; r <= prm.t_max_idle + 1; ++r) {
                     const int64_t span = (int64_t)r * d;
                     if (q + 1 >= t_begin && q + 1 > last_end_ && q + span <= t_end - 1) spec_ext(q + 1, q + span, 1);
@@ -843,9 +856,9 @@ private:
     GridCache grid_;
     ExtCache ext_;
     uint32_t round_ = 0;
-    FlatCache spec_starts_;   // climb starts whose windows were asked speculatively
-    FlatCache ext_left_;      // window starts whose left extension windows were asked ahead
-    FlatCache ext_right_;     // window ends whose right extension windows were asked ahead
+    PosSet spec_starts_;   // climb starts whose windows were asked speculatively
+    PosSet ext_left_;      // window starts whose left extension windows were asked ahead
+    PosSet ext_right_;     // window ends whose right extension windows were asked ahead
     int32_t next_chain_ = 0;
 };
 
