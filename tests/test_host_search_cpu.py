@@ -205,3 +205,93 @@ def test_random_configurations(driver, tmp_path, pairs, seed):
             ref, n_ref = (O.search_td if mode == 0 else O.search_bu)(
                 x, y, t_begin=t_begin, t_end=t_end, estimator=est, **kw)
             _same(g, ref, n_ref)
+
+
+def _serve_queries(rng, n_queries, n):
+    qs = []
+    for i in range(n_queries):
+        qs.append(dict(pair=i % 2, mode=int(rng.integers(0, 2)), tb=int(rng.integers(0, 300)),
+                       te=int(rng.integers(n - 300, n + 1)), k=int(rng.choice([3, 4])), s_min=32,
+                       s_max=int(rng.choice([128, 256])), pruning=int(rng.integers(0, 2)),
+                       seed=int(rng.integers(0, 1 << 30)), est=int(rng.integers(0, 4) == 0),
+                       cancel=int(i == 5)))
+    return qs
+
+
+def _check_served(exe, tmp_path, pairs, seed):
+    rng = np.random.default_rng(seed)
+    qs = _serve_queries(rng, 14, len(pairs[0][0]))
+    series = _series_file(tmp_path, pairs)
+    qfile = os.path.join(str(tmp_path), "queries.txt")
+    with open(qfile, "w") as f:
+        for q in qs:
+            f.write("%d %d %d %d %d %d %d %d %d %d %d\n" % (
+                q["pair"], q["mode"], q["tb"], q["te"], q["k"], q["s_min"], q["s_max"],
+                q["pruning"], q["seed"], q["est"], q["cancel"]))
+    out = subprocess.run([exe, series, qfile], capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, (out.stdout[-500:], out.stderr[-3000:])
+    assert "ThreadSanitizer" not in out.stderr, out.stderr[-3000:]
+    res, cur = {}, None
+    for line in out.stdout.splitlines():
+        f = line.split()
+        if f[0] == "Q":
+            cur = int(f[1])
+            res[cur] = (int(f[2]), [])
+        elif f[0] == "W":
+            res[cur][1].append((int(f[1]), int(f[2]), float(f[3]), float(f[4])))
+    assert sorted(res) == list(range(len(qs)))
+    for i, q in enumerate(qs):
+        st, got = res[i]
+        if q["cancel"] and st != 0:
+            continue   # cancelled before it finished
+        assert st == 0, (i, st)
+        x, y = pairs[q["pair"]]
+        ref, _ = (O.search_td if q["mode"] == 0 else O.search_bu)(
+            x, y, t_begin=q["tb"], t_end=q["te"], k=q["k"], s_min=q["s_min"], s_max=q["s_max"],
+            pruning=q["pruning"], seed=q["seed"], estimator=q["est"])
+        assert got == list(ref), i
+
+
+def _build_serve(sanitize):
+    from paper_2204_09131_gb300 import build as B
+    try:
+        nvcc = B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    os.makedirs(BUILD, exist_ok=True)
+    tag = "_tsan" if sanitize else ""
+    flags = ["-fsanitize=thread"] if sanitize else []
+    objs = []
+    for src in (os.path.join(HERE, "host_search", "host_serve_main.cu"), os.path.join(B.CSRC, "serve.cu"),
+                os.path.join(B.CSRC, "search.cu")):
+        obj = os.path.join(BUILD, "serve%s_%s.o" % (tag, os.path.basename(src)[:-3]))
+        cmd = [nvcc, *B.ARCH, "-O1", "-g", "-std=c++17", "--expt-relaxed-constexpr",
+               "-I" + B.INCLUDE, "-I" + B.CSRC, "-c", src, "-o", obj]
+        if sanitize:
+            cmd += ["-Xcompiler", "-fsanitize=thread"]
+        subprocess.run(cmd, check=True, capture_output=True)
+        objs.append(obj)
+    orc = os.path.join(BUILD, "oracle%s.o" % tag)
+    subprocess.run(["gcc", "-O1", "-g", *flags, "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-c",
+                    os.path.join(ROOT, "oracle", "isycos_oracle.c"), "-o", orc], check=True)
+    exe = os.path.join(BUILD, "host_serve%s" % tag)
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    link = subprocess.run(["g++", *flags, *objs, orc, "-o", exe, "-L" + cudalib, "-lcudart_static",
+                           "-ldl", "-lpthread", "-lrt", "-lm"], capture_output=True, text=True)
+    if link.returncode != 0:
+        if sanitize:
+            pytest.skip("no ThreadSanitizer runtime: " + link.stderr[-200:])
+        raise AssertionError(link.stderr[-2000:])
+    return exe
+
+
+def test_served_queries_match_oracle(tmp_path, pairs):
+    """The serving loop (csrc/serve.cu: admission with fewer slots than queries, four worker
+    lanes, submissions from two threads, a cancellation) returns every query's own search."""
+    _check_served(_build_serve(False), tmp_path, pairs, 21)
+
+
+def test_serving_threads_race_free(tmp_path, pairs):
+    """The same under ThreadSanitizer: the server's threads, the submitting threads and the
+    pollers share no unsynchronised state."""
+    _check_served(_build_serve(True), tmp_path, pairs, 22)
