@@ -7,7 +7,9 @@
 // with the oracle's searches without a GPU, and the host threads can run under a race
 // detector.
 //
-// usage: host_serve <series file> <queries file>
+// usage: host_serve <series file> <queries file> [batch]
+//   batch: run all queries in one isycos_search_queries call (engine lanes on host threads,
+//   SYCOS_TD queries on lanes of their own) instead of serving them
 //   series file: as for host_search
 //   queries file: one query per line: pair mode t_begin t_end k s_min s_max pruning seed
 //                 estimator cancel(0/1)
@@ -107,6 +109,8 @@ extern "C" isycos_status isycos_serve_submit(isycos_ctx *, int32_t, int32_t, int
 extern "C" isycos_status isycos_serve_poll(isycos_ctx *, uint64_t, isycos_result_window *, int64_t,
                                            int64_t *, double *);
 extern "C" isycos_status isycos_serve_cancel(isycos_ctx *, uint64_t);
+extern "C" isycos_status isycos_search_queries(isycos_ctx *, int64_t, const isycos_query *,
+                                               isycos_result_window *, int64_t, int64_t *);
 
 int main(int argc, char **argv) {
     if (argc < 3) return 2;
@@ -174,6 +178,26 @@ int main(int argc, char **argv) {
     }
     fclose(qf);
 
+    if (argc > 3 && strcmp(argv[3], "batch") == 0) {
+        ctx->max_lanes = 8;
+        std::vector<isycos_query> qa(qs.size());
+        for (size_t i = 0; i < qs.size(); ++i)
+            qa[i] = isycos_query{2 * qs[i].pair, 2 * qs[i].pair + 1, qs[i].tb, qs[i].te, qs[i].prm};
+        const int64_t cap = 4096;
+        std::vector<isycos_result_window> out(qs.size() * (size_t)cap);
+        std::vector<int64_t> n_out(qs.size());
+        const isycos_status st = isycos_search_queries(ctx.get(), (int64_t)qs.size(), qa.data(),
+                                                       out.data(), cap, n_out.data());
+        for (size_t i = 0; i < qs.size(); ++i) {
+            printf("Q %zu %d %lld\n", i, (int)st, (long long)(st == ISYCOS_OK ? n_out[i] : 0));
+            if (st == ISYCOS_OK)
+                for (int64_t w = 0; w < n_out[i]; ++w) {
+                    const isycos_result_window &r = out[i * (size_t)cap + (size_t)w];
+                    printf("W %lld %lld %.17g %.17g\n", (long long)r.t_s, (long long)r.t_e, r.score, r.mi);
+                }
+        }
+        return 0;
+    }
     // submit from two threads at once, then poll every query to completion
     std::thread t2([&] {
         for (size_t i = 1; i < qs.size(); i += 2)

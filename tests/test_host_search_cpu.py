@@ -218,7 +218,7 @@ def _serve_queries(rng, n_queries, n):
     return qs
 
 
-def _check_served(exe, tmp_path, pairs, seed):
+def _check_served(exe, tmp_path, pairs, seed, batch=False):
     rng = np.random.default_rng(seed)
     qs = _serve_queries(rng, 14, len(pairs[0][0]))
     series = _series_file(tmp_path, pairs)
@@ -228,7 +228,8 @@ def _check_served(exe, tmp_path, pairs, seed):
             f.write("%d %d %d %d %d %d %d %d %d %d %d\n" % (
                 q["pair"], q["mode"], q["tb"], q["te"], q["k"], q["s_min"], q["s_max"],
                 q["pruning"], q["seed"], q["est"], q["cancel"]))
-    out = subprocess.run([exe, series, qfile], capture_output=True, text=True, timeout=900)
+    out = subprocess.run([exe, series, qfile] + (["batch"] if batch else []), capture_output=True,
+                         text=True, timeout=900)
     if "FATAL: ThreadSanitizer" in out.stderr:   # the sanitizer cannot start on this system
         pytest.skip(out.stderr.strip().splitlines()[0][:200])
     assert out.returncode == 0, (out.stdout[-500:], out.stderr[-3000:])
@@ -244,7 +245,7 @@ def _check_served(exe, tmp_path, pairs, seed):
     assert sorted(res) == list(range(len(qs)))
     for i, q in enumerate(qs):
         st, got = res[i]
-        if q["cancel"] and st != 0:
+        if q["cancel"] and st != 0 and not batch:
             continue   # cancelled before it finished
         assert st == 0, (i, st)
         x, y = pairs[q["pair"]]
@@ -306,3 +307,9 @@ def test_serving_threads_race_free(tmp_path, pairs):
     """The same under ThreadSanitizer: the server's threads, the submitting threads and the
     pollers share no unsynchronised state."""
     _check_served(_build_serve(True), tmp_path, pairs, 22)
+
+
+def test_search_queries_lanes_match_oracle_race_free(tmp_path, pairs):
+    """isycos_search_queries with TD and BU queries in one call (engine lanes on host threads,
+    TD lanes apart) under ThreadSanitizer: every query's windows are its own search's."""
+    _check_served(_build_serve(True), tmp_path, pairs, 23, batch=True)
