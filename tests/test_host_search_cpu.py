@@ -313,3 +313,53 @@ def test_search_queries_lanes_match_oracle_race_free(tmp_path, pairs):
     """isycos_search_queries with TD and BU queries in one call (engine lanes on host threads,
     TD lanes apart) under ThreadSanitizer: every query's windows are its own search's."""
     _check_served(_build_serve(True), tmp_path, pairs, 23, batch=True)
+
+
+def test_search_machines_memory_safe(tmp_path, pairs):
+    """The search machines under AddressSanitizer and UndefinedBehaviorSanitizer: no invalid
+    access and no undefined behaviour in TD, BU (speculation off and at 64 climbs, a step that
+    leaves the lattice, long idle limits), selection or chunks, and the oracle's windows."""
+    from paper_2204_09131_gb300 import build as B
+    try:
+        nvcc = B.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    os.makedirs(BUILD, exist_ok=True)
+    san = ["-fsanitize=address", "-fsanitize=undefined", "-fno-omit-frame-pointer"]
+    objs = []
+    for src in (SRC, os.path.join(B.CSRC, "search.cu")):
+        obj = os.path.join(BUILD, "asan_%s.o" % os.path.basename(src)[:-3])
+        cmd = [nvcc, *B.ARCH, "-O1", "-g", "-std=c++17", "--expt-relaxed-constexpr", "-I" + B.INCLUDE,
+               "-I" + B.CSRC, "-c", src, "-o", obj]
+        for flag in san:
+            cmd += ["-Xcompiler", flag]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.skip("cannot build with the sanitizers: " + r.stderr[-200:])
+        objs.append(obj)
+    orc = os.path.join(BUILD, "asan_oracle.o")
+    r = subprocess.run(["gcc", "-O1", "-g", *san, "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-c",
+                        os.path.join(ROOT, "oracle", "isycos_oracle.c"), "-o", orc], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("cannot build with the sanitizers: " + r.stderr[-200:])
+    exe = os.path.join(BUILD, "host_search_asan")
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    r = subprocess.run(["g++", "-fsanitize=address", "-fsanitize=undefined", *objs, orc, "-o", exe,
+                        "-L" + cudalib, "-lcudart_static", "-ldl", "-lpthread", "-lrt", "-lm"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no sanitizer runtime: " + r.stderr[-200:])
+    path = _series_file(tmp_path, pairs)
+    cases = [dict(mode=1, pruning=1, seed=31, spec=0, incremental=2),
+             dict(mode=1, pruning=1, seed=10, spec=64, t_begin=300, t_end=1700),
+             dict(mode=1, pruning=1, delta_bu=5, t_max_idle=10, seed=4),
+             dict(mode=0, pruning=1, delta_td=7, estimator=1),
+             dict(mode=2, pruning=1, sel_partitions=6, sel_samples=2, s_max=128),
+             dict(mode=1, pruning=1, chunks=3, s_max=128)]
+    for kw in cases:
+        args = [exe, path] + ["%s=%s" % kv for kv in kw.items()]
+        if "s_max" not in kw:
+            args.append("s_max=256")
+        out = subprocess.run(args, capture_output=True, text=True, timeout=900)
+        assert "AddressSanitizer" not in out.stderr and "runtime error" not in out.stderr, out.stderr[-3000:]
+        assert out.returncode == 0, (kw, out.stderr[-2000:])
