@@ -255,7 +255,16 @@ def _check_served(exe, tmp_path, pairs, seed, batch=False):
         assert got == list(ref), i
 
 
+_SERVE_BUILDS = {}
+
+
 def _build_serve(sanitize):
+    if sanitize not in _SERVE_BUILDS:   # built once per session and flavour
+        _SERVE_BUILDS[sanitize] = _build_serve_now(sanitize)
+    return _SERVE_BUILDS[sanitize]
+
+
+def _build_serve_now(sanitize):
     from paper_2204_09131_gb300 import build as B
     try:
         nvcc = B.nvcc()
