@@ -407,7 +407,6 @@ public:
         c_ = t_begin;
         last_end_ = t_begin - 1;
         L_.assign(prm.h, 0.0);
-        cand_.reserve((size_t)8 * (prm.t_max_idle + 1));
         ring_ext_.assign((size_t)2 * (prm.t_max_idle + 2), RingExt{});
         ext_.init(prm.delta_bu, prm.t_max_idle + 1);
         spec_starts_.init(prm.delta_bu);
@@ -558,11 +557,6 @@ private:
             x.have = true;
             x.v = v;
         }
-    };
-    // Candidates of the ring being decided, in the decision order.
-    struct Cand {
-        int64_t ts, te;
-        Val v;
     };
     // Score of the extension window (s, m) last delivered for a ring and side.
     struct RingExt {
@@ -756,8 +750,15 @@ private:
     bool decide(int r) {
         int64_t ac, bc;
         grid_.centre(ws_, we_, &ac, &bc);
-        cand_.clear();
-        int pure[2] = {-1, -1};   // candidates (-r, 0) and (0, r): the pure extensions
+        // One pass over the ring: the best candidate, the pure extensions' scores and the
+        // counts to add, committed only once every score is at hand (the counts are whole
+        // numbers far below 2^53, so their sums do not depend on the order).
+        bool have = false;
+        int64_t bs = 0, be = 0, n_read = 0;
+        double pairs_read = 0.0;
+        Val bv{0.0, 0.0};
+        bool pure[2] = {false, false};   // candidates (-r, 0) and (0, r): the pure extensions
+        double pure_sc[2] = {0.0, 0.0};
         for (int64_t a = -r; a <= r; ++a)
             // the perimeter of the square, b ascending within each a
             for (int64_t b = -r; b <= r; b += (a == -r || a == r) ? 1 : 2 * r) {
@@ -765,9 +766,23 @@ private:
                 if (!keep(a, b, r, dropped_[0], dropped_[1], &ts, &te)) continue;
                 Val v;
                 if (!grid_.get(ac + a, bc + b, &v)) return false;
-                if (a == -r && b == 0) pure[0] = (int)cand_.size();
-                if (a == 0 && b == r) pure[1] = (int)cand_.size();
-                cand_.push_back(Cand{ts, te, v});
+                const int64_t m = te - ts + 1;
+                ++n_read;
+                pairs_read += (double)m * (double)(m - 1);
+                if (!have || v.score > bv.score) {        // first maximum wins
+                    have = true;
+                    bs = ts;
+                    be = te;
+                    bv = v;
+                }
+                if (a == -r && b == 0) {
+                    pure[0] = true;
+                    pure_sc[0] = v.score;
+                }
+                if (a == 0 && b == r) {
+                    pure[1] = true;
+                    pure_sc[1] = v.score;
+                }
             }
         // the noise test's extension windows (Def. 6.2): the r delta points added on that side
         const bool test = prm.pruning && (int64_t)r * prm.delta_bu >= prm.k + 1;
@@ -776,29 +791,19 @@ private:
             const int64_t span = (int64_t)r * prm.delta_bu;
             const int64_t es[2] = {ws_ - span, we_ + 1};
             for (int sd = 0; sd < 2; ++sd)
-                if (pure[sd] >= 0 && !ext_score(r, sd, es[sd], span, &ext[sd])) return false;
+                if (pure[sd] && !ext_score(r, sd, es[sd], span, &ext[sd])) return false;
         }
         // every score is at hand: the step
-        bool have = false;
-        int64_t bs = 0, be = 0;
-        Val bv{0.0, 0.0};
-        for (const Cand &c : cand_) {
-            count(c.te - c.ts + 1);
-            if (!have || c.v.score > bv.score) {        // first maximum wins
-                have = true;
-                bs = c.ts;
-                be = c.te;
-                bv = c.v;
-            }
-        }
+        evals += n_read;
+        cost += pairs_read;
         if (prm.pruning) {
             for (int sd = 0; sd < 2; ++sd) {
-                if (pure[sd] < 0) continue;
+                if (!pure[sd]) continue;
                 bool noise = false;
                 if (test) {
                     count((int64_t)r * prm.delta_bu);
                     // Def. 6.2 with w = current window, w' = extension, w'' = the neighbour.
-                    noise = (Iw_ > 0.0) && (ext[sd].score < prm.tau) && (cand_[pure[sd]].v.score < Iw_);
+                    noise = (Iw_ > 0.0) && (ext[sd].score < prm.tau) && (pure_sc[sd] < Iw_);
                 }
                 run_[sd] = noise ? run_[sd] + 1 : 0;
                 if (run_[sd] >= prm.p) dropped_[sd] = true;
@@ -849,7 +854,6 @@ private:
     uint64_t step_ = 0, climb_ = 0;
     int run_[2] = {0, 0};
     bool dropped_[2] = {false, false};
-    std::vector<Cand> cand_;
     std::vector<RingExt> ring_ext_;
     bool stuck_ = false;
     std::vector<Dest> dest_;
