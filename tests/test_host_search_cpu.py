@@ -233,7 +233,8 @@ def _check_served(exe, tmp_path, pairs, seed, batch=False):
     if "FATAL: ThreadSanitizer" in out.stderr:   # the sanitizer cannot start on this system
         pytest.skip(out.stderr.strip().splitlines()[0][:200])
     assert out.returncode == 0, (out.stdout[-500:], out.stderr[-3000:])
-    assert "ThreadSanitizer" not in out.stderr, out.stderr[-3000:]
+    for report in ("ThreadSanitizer", "AddressSanitizer", "runtime error"):
+        assert report not in out.stderr, out.stderr[-3000:]
     res, cur = {}, None
     for line in out.stdout.splitlines():
         f = line.split()
@@ -256,72 +257,84 @@ def _check_served(exe, tmp_path, pairs, seed, batch=False):
 
 
 _SERVE_BUILDS = {}
+_SANITIZERS = {"": [], "tsan": ["-fsanitize=thread"],
+               "asan": ["-fsanitize=address", "-fsanitize=undefined", "-fno-omit-frame-pointer"]}
 
 
-def _build_serve(sanitize):
-    if sanitize not in _SERVE_BUILDS:   # built once per session and flavour
-        _SERVE_BUILDS[sanitize] = _build_serve_now(sanitize)
-    return _SERVE_BUILDS[sanitize]
+def _build_serve(flavour):
+    if flavour not in _SERVE_BUILDS:   # built once per session and flavour
+        _SERVE_BUILDS[flavour] = _build_serve_now(flavour)
+    return _SERVE_BUILDS[flavour]
 
 
-def _build_serve_now(sanitize):
+def _build_serve_now(flavour):
     from paper_2204_09131_gb300 import build as B
     try:
         nvcc = B.nvcc()
     except RuntimeError:
         pytest.skip("nvcc not available")
     os.makedirs(BUILD, exist_ok=True)
-    tag = "_tsan" if sanitize else ""
-    flags = ["-fsanitize=thread"] if sanitize else []
+    tag = "_" + flavour if flavour else ""
+    flags = _SANITIZERS[flavour]
+
+    def failed(what, err):
+        if flavour:   # the sanitizer may be missing here: skip rather than fail
+            pytest.skip("cannot build with %s (%s): %s" % (flavour, what, err[-200:]))
+        raise AssertionError(err[-2000:])
+
     objs = []
     for src in (os.path.join(HERE, "host_search", "host_serve_main.cu"), os.path.join(B.CSRC, "serve.cu"),
                 os.path.join(B.CSRC, "search.cu")):
         obj = os.path.join(BUILD, "serve%s_%s.o" % (tag, os.path.basename(src)[:-3]))
         cmd = [nvcc, *B.ARCH, "-O1", "-g", "-std=c++17", "--expt-relaxed-constexpr",
                "-I" + B.INCLUDE, "-I" + B.CSRC, "-c", src, "-o", obj]
-        if sanitize:
-            cmd += ["-Xcompiler", "-fsanitize=thread"]
+        for flag in flags:
+            cmd += ["-Xcompiler", flag]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            if sanitize:
-                pytest.skip("cannot build with ThreadSanitizer: " + r.stderr[-200:])
-            raise AssertionError(r.stderr[-2000:])
+            failed("compile", r.stderr)
         objs.append(obj)
     orc = os.path.join(BUILD, "oracle%s.o" % tag)
     r = subprocess.run(["gcc", "-O1", "-g", *flags, "-fno-fast-math", "-ffp-contract=off", "-std=c11",
                         "-c", os.path.join(ROOT, "oracle", "isycos_oracle.c"), "-o", orc],
                        capture_output=True, text=True)
     if r.returncode != 0:
-        if sanitize:
-            pytest.skip("cannot build with ThreadSanitizer: " + r.stderr[-200:])
-        raise AssertionError(r.stderr[-2000:])
+        failed("compile", r.stderr)
     exe = os.path.join(BUILD, "host_serve%s" % tag)
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    link = subprocess.run(["g++", *flags, *objs, orc, "-o", exe, "-L" + cudalib, "-lcudart_static",
-                           "-ldl", "-lpthread", "-lrt", "-lm"], capture_output=True, text=True)
+    link = subprocess.run(["g++", *[f for f in flags if f.startswith("-fsanitize")], *objs, orc, "-o", exe,
+                           "-L" + cudalib, "-lcudart_static", "-ldl", "-lpthread", "-lrt", "-lm"],
+                          capture_output=True, text=True)
     if link.returncode != 0:
-        if sanitize:
-            pytest.skip("no ThreadSanitizer runtime: " + link.stderr[-200:])
-        raise AssertionError(link.stderr[-2000:])
+        failed("link", link.stderr)
     return exe
 
 
 def test_served_queries_match_oracle(tmp_path, pairs):
     """The serving loop (csrc/serve.cu: admission with fewer slots than queries, four worker
     lanes, submissions from two threads, a cancellation) returns every query's own search."""
-    _check_served(_build_serve(False), tmp_path, pairs, 21)
+    _check_served(_build_serve(""), tmp_path, pairs, 21)
 
 
 def test_serving_threads_race_free(tmp_path, pairs):
     """The same under ThreadSanitizer: the server's threads, the submitting threads and the
     pollers share no unsynchronised state."""
-    _check_served(_build_serve(True), tmp_path, pairs, 22)
+    _check_served(_build_serve("tsan"), tmp_path, pairs, 22)
 
 
 def test_search_queries_lanes_match_oracle_race_free(tmp_path, pairs):
     """isycos_search_queries with TD and BU queries in one call (engine lanes on host threads,
     TD lanes apart) under ThreadSanitizer: every query's windows are its own search's."""
-    _check_served(_build_serve(True), tmp_path, pairs, 23, batch=True)
+    _check_served(_build_serve("tsan"), tmp_path, pairs, 23, batch=True)
+
+
+def test_serving_memory_safe(tmp_path, pairs):
+    """The serving loop and isycos_search_queries under AddressSanitizer and
+    UndefinedBehaviorSanitizer: no invalid access, leak or undefined behaviour in admission,
+    the worker lanes, cancellation or the batched call, and every result still the oracle's."""
+    exe = _build_serve("asan")
+    _check_served(exe, tmp_path, pairs, 24)
+    _check_served(exe, tmp_path, pairs, 25, batch=True)
 
 
 def test_search_machines_memory_safe(tmp_path, pairs):
