@@ -35,6 +35,13 @@
  *     int64, so that the sums are exact and independent of summation order; the
  *     oracle also reports the plain binary64 evaluation of Eq. KSGmi ("exact").
  *
+ * Pins: the estimator against the Sec. 7.1 example, hand-worked windows, independent
+ * brute forces and closed forms; the searches against hand-traced score tables (layers,
+ * partitions, noise skips, rings, acceptance, ties, restarts, one-sided pruning).
+ * Parity unpinned: the LAHC history stream of SYCOS_BU beyond its SplitMix64 reference
+ * outputs, the chunk semantics of Algorithm 4 and the deterministic runtime and sampling
+ * of Algorithm 3; the paper gives no numbers or examples for them.
+ *
  * Build: gcc -O2 -fno-fast-math -ffp-contract=off -shared -fPIC (no flush-to-zero).
  */
 #include <math.h>
@@ -64,7 +71,15 @@ enum {
     ORC_MUT_TIE_LATE = 6,        /* break distance ties toward the larger index    */
     ORC_MUT_EUCLID = 7,          /* Euclidean instead of max-norm distance         */
     ORC_MUT_H_SIGN = 8,          /* keep the garbled sign of the entropy formula   */
-    ORC_MUT_PSI_M_MINUS = 9      /* use psi(m - 1) in place of psi(m)              */
+    ORC_MUT_PSI_M_MINUS = 9,     /* use psi(m - 1) in place of psi(m)              */
+    /* the searches' readings */
+    ORC_MUT_ACCEPT_GE = 10,      /* Alg. 2 acceptance with >= instead of >         */
+    ORC_MUT_TIE_LAST = 11,       /* the last maximum of a ring wins                */
+    ORC_MUT_TD_NO_CLAMP = 12,    /* reduce(s_w) = s_w / 2 without the s_min floor  */
+    ORC_MUT_TD_DELTA_OVERLAP = 13, /* w_delta = [t_e0, t_e1], one point in w_o too */
+    ORC_MUT_NOISE_NO_IO = 14,    /* Def. 6.2 without its I_w > 0 condition         */
+    ORC_MUT_BU_SQUARE = 15,      /* evaluate the whole square, not the ring N_r    */
+    ORC_MUT_BU_DROP_BOTH = 16    /* a noisy side drops both sides' neighbours      */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -452,6 +467,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                     /* w = w_o (overlap with the previous window) followed by w_delta (new data). */
                     int64_t o_s = t, o_e = t + s_w - delta - 1;
                     int64_t d_s = t + s_w - delta, d_e = t + s_w - 1;
+                    if (g_mutation == ORC_MUT_TD_DELTA_OVERLAP) d_s -= 1;
                     if (o_e - o_s + 1 >= p->k + 1 && d_e - d_s + 1 >= p->k + 1) {
                         double so, mo, sd, md;
                         rc = f(user, o_s, o_e, &so, &mo);
@@ -460,7 +476,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                         if (rc) break;
                         evals += 2;
                         /* Def. 6.2 with w = w_o, w' = w_delta, w'' = w: requires I_{w_o} > 0. */
-                        noise = (so > 0.0) && (sd < p->tau) && (sc < so);
+                        noise = (so > 0.0 || g_mutation == ORC_MUT_NOISE_NO_IO) && (sd < p->tau) && (sc < so);
                     }
                 }
                 noise_run = noise ? noise_run + 1 : 0;
@@ -479,7 +495,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
         if (rc) { free(S.v); return rc; }
         if (s_w <= p->s_min) break;
         s_w = s_w / 2;                         /* reduce(s_w) */
-        if (s_w < p->s_min) s_w = p->s_min;
+        if (s_w < p->s_min && g_mutation != ORC_MUT_TD_NO_CLAMP) s_w = p->s_min;
     }
     if (n_evals) *n_evals = evals;
     rc = orc_emit(&S, out, cap, n_out);
@@ -536,7 +552,7 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
             for (int64_t a = -r; a <= r && rc == ORC_OK; ++a) {
                 for (int64_t b = -r; b <= r; ++b) {
                     int64_t aa = a < 0 ? -a : a, ab = b < 0 ? -b : b;
-                    if ((aa > ab ? aa : ab) != r) continue;     /* ring N_r only */
+                    if ((aa > ab ? aa : ab) != r && g_mutation != ORC_MUT_BU_SQUARE) continue;     /* ring N_r only */
                     if (dropped[0] && a < 0) continue;
                     if (dropped[1] && b > 0) continue;
                     int64_t ts = ws + a * delta, te = we + b * delta;
@@ -547,7 +563,7 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                     rc = f(user, ts, te, &sc, &mi);
                     if (rc) break;
                     ++evals;
-                    if (!have_best || sc > bsc) {          /* first maximum wins */
+                    if (!have_best || sc > bsc || (g_mutation == ORC_MUT_TIE_LAST && sc == bsc)) {   /* first maximum wins */
                         have_best = 1; bs = ts; be = te; bsc = sc; bmi = mi;
                     }
                     if (a == -r && b == 0) { have_ext[0] = 1; ext_sc[0] = sc; }
@@ -567,15 +583,20 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                         if (rc) break;
                         ++evals;
                         /* Def. 6.2 with w = current window, w' = extension, w'' = neighbour. */
-                        noise = (Iw > 0.0) && (sd < p->tau) && (ext_sc[side] < Iw);
+                        noise = (Iw > 0.0 || g_mutation == ORC_MUT_NOISE_NO_IO) && (sd < p->tau) && (ext_sc[side] < Iw);
                     }
                     noise_run[side] = noise ? noise_run[side] + 1 : 0;
-                    if (noise_run[side] >= pcount) dropped[side] = 1;
+                    if (noise_run[side] >= pcount) {
+                        dropped[side] = 1;
+                        if (g_mutation == ORC_MUT_BU_DROP_BOTH) dropped[1 - side] = 1;
+                    }
                 }
                 if (rc) break;
             }
             int32_t v = (int32_t)(orc_splitmix64_at(p->seed, (climb << 32) + step + 1) % (uint64_t)h);
-            if (have_best && (bsc > L[v] || bsc > Iw)) {
+            int better = (bsc > L[v] || bsc > Iw);
+            if (g_mutation == ORC_MUT_ACCEPT_GE) better = (bsc >= L[v] || bsc >= Iw);
+            if (have_best && better) {
                 ws = bs; we = be; Iw = bsc; mw = bmi;
                 t_idle = 0;
             } else {

@@ -37,6 +37,13 @@ MUTATIONS = {
     "euclid": 7,
     "h_sign": 8,
     "psi_m_minus": 9,
+    "accept_ge": 10,
+    "tie_last": 11,
+    "td_no_clamp": 12,
+    "td_delta_overlap": 13,
+    "noise_no_io": 14,
+    "bu_square": 15,
+    "bu_drop_both": 16,
 }
 
 

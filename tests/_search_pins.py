@@ -1,0 +1,190 @@
+"""Hand-traced pins of the oracle's searches (SYCOS_TD, Algorithm 1; SYCOS_BU, Algorithm 2;
+the noise pruning of Sec. 6) on mocked score tables.
+
+The paper prints no numbers for its searches, so each pin fixes one reading of the text by
+a trace worked out by hand in its comment: which windows are scored, in which order, and
+what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
+
+- ``pin_td_layers``: layer sizes s_max, s_max / 2, ..., the step delta = max(k + 1, s_w / 4),
+  uncorrelated partitions and the literal partition end of Algorithm 1;
+- ``pin_td_size_floor``: reduce(s_w) stops at s_min (a layer of s_min points, not s_w / 2);
+- ``pin_td_noise_skip``: w_o = [t_s1, t_e0], w_delta = [t_e0 + 1, t_e1] and the skip after p
+  detections (Def. 6.2 in SYCOS_TD);
+- ``pin_td_noise_needs_positive_overlap``: Def. 6.2 only holds when I_{w_o} > 0;
+- ``pin_bu_single_peak``: a climb over a single-peak table;
+- ``pin_bu_plateau``: the ring N_1 (not the whole square), strict acceptance of Algorithm 2,
+  and the next climb starting at max(t_e + 1, c + s_min);
+- ``pin_bu_first_maximum``: the first maximum of a ring, a outer and b inner, wins;
+- ``pin_bu_restart_after_left_move``: a climb that ends left of its start does not move the
+  next start back;
+- ``pin_bu_noise_drops_one_side``: a noisy extension drops only the neighbours that extend
+  that side.
+
+tests/test_oracle_mutations.py runs them against planted mistakes of the oracle's searches.
+"""
+from __future__ import annotations
+
+from oracle import oracle as O
+
+
+def _score(table, log=None, default=0.0):
+    """A window score from a dict {(t_s, t_e): score} or a function (t_s, t_e) -> score; every
+    call is appended to ``log``."""
+    def score(ts, te):
+        if log is not None:
+            log.append((ts, te))
+        v = table(ts, te) if callable(table) else table.get((ts, te), default)
+        return v, v
+    return score
+
+
+def _spans(wins):
+    return [(a, b) for a, b, _, _ in wins]
+
+
+def pin_td_layers():
+    # Correlated iff the window lies inside [20, 40).  Range [0, 48), s_max 16, s_min 8,
+    # k = 1 so delta = max(k+1, s_w/4) = 4 then 2.
+    # Layer 16: starts 0,4,8,12,16 uncorrelated, [20,35] correlated, next start 36 does
+    # not fit.  Layer 8: partitions [0,19] (starts 0..12 step 2) and [36,47] (36,38,40).
+    log = []
+    score = _score(lambda ts, te: 1.0 if ts >= 20 and te < 40 else 0.0, log)
+    wins, n = O.search_td(score, t_begin=0, t_end=48, k=1, s_min=8, s_max=16, sigma=0.5)
+    assert _spans(wins) == [(20, 35)], wins
+    assert n == 16 and len(log) == 16, (n, log)
+    assert log[:6] == [(t, t + 15) for t in (0, 4, 8, 12, 16, 20)], log
+    assert log[6:] == [(t, t + 7) for t in range(0, 13, 2)] + [(36, 43), (38, 45), (40, 47)], log
+
+
+def pin_td_size_floor():
+    # Nothing is correlated on [0, 48); s_max 24, s_min 16, k = 1.  Layer 24: delta = 6,
+    # starts 0..24.  reduce(24) = 12 is below s_min, so the second and last layer has 16
+    # points: delta = 4, starts 0..32.
+    log = []
+    wins, n = O.search_td(_score(lambda ts, te: 0.0, log), t_begin=0, t_end=48, k=1, s_min=16,
+                          s_max=24, sigma=0.5)
+    assert wins == [] and n == 14, (wins, n)
+    assert log == [(t, t + 23) for t in range(0, 25, 6)] + [(t, t + 15) for t in range(0, 33, 4)], log
+
+
+def pin_td_noise_skip():
+    # One layer of size 16, delta 4, p = 2, sigma 0.5, tau 0.1.  Windows [4,19] and
+    # [8,23] are each noise w.r.t. their overlap (I_delta < tau and I_w < I_o), so after
+    # the second detection the scan jumps to t_e + 1 = 24, where [24,39] is correlated.
+    table = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
+             (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.05, (24, 39): 0.6}
+    log = []
+    wins, n = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
+                          delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
+    assert _spans(wins) == [(24, 39)], wins
+    assert log == [(0, 15), (4, 19), (4, 15), (16, 19), (8, 23), (8, 19), (20, 23), (24, 39)], log
+    # Without pruning the scan shifts through 12, 16, 20 before reaching 24.
+    log2 = []
+    wins2, _ = O.search_td(_score(table, log2), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
+                           delta_td=4, sigma=0.5, tau=0.1, p=2)
+    assert _spans(wins2) == [(24, 39)], wins2
+    assert log2 == [(t, t + 15) for t in range(0, 25, 4)], log2
+
+
+def pin_td_noise_needs_positive_overlap():
+    # As above with p = 1, but the overlap [4,15] of the shifted window [4,19] scores 0: with
+    # I_{w_o} = 0, Def. 6.2 does not hold even though I_delta = 0.05 < tau and I_w = -0.1 <
+    # I_{w_o}, so the layer keeps shifting by 4 (every other window scores 0 and is never
+    # noise) through the last start 32.
+    table = {(0, 15): 0.2, (4, 19): -0.1, (4, 15): 0.0, (16, 19): 0.05}
+    log = []
+    wins, _ = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
+                          delta_td=4, sigma=0.5, tau=0.1, p=1, pruning=1)
+    assert wins == [], wins
+    assert [w for w in log if w[1] - w[0] + 1 == 16] == [(t, t + 15) for t in range(0, 33, 4)], log
+
+
+def pin_bu_single_peak():
+    # Score 1 - (|t_s - 20| + |t_e - 39|) / 100: a single peak at [20, 39].  From
+    # w0 = [0, 7] the climb moves both ends by delta = 4 until t_s = 20, then the end
+    # until 39, where every ring-1 neighbour is worse (T_maxIdle = 0 stops the climb).
+    score = _score(lambda ts, te: 1.0 - (abs(ts - 20) + abs(te - 39)) / 100.0)
+    wins, _ = O.search_bu(score, t_begin=0, t_end=100, k=1, s_min=8, s_max=40, delta_bu=4,
+                          h=1, t_max_idle=0, sigma=0.9, seed=3)
+    assert _spans(wins) == [(20, 39)], wins
+    assert abs(wins[0][2] - 1.0) < 1e-12, wins
+
+
+def pin_bu_plateau():
+    # Every window scores 0.5; range [0, 24), s_min 8, s_max 16, delta 4, h = 1, T_maxIdle 0,
+    # sigma 0.4.  Climb 0 from [0,7]: of ring N_1 only [0,11] (a=0, b=1) and [4,11] (a=1,
+    # b=1) have 8..16 points inside the range; neither beats 0.5 strictly, so the climb ends
+    # where it started and [0,7] is kept.  The next climb starts at max(7 + 1, 0 + 8) = 8:
+    # its ring has [8,19] and [12,19] (a = -1 would start at 4 <= 7).  The last climb at
+    # [16,23] has no neighbour inside the range.
+    log = []
+    wins, n = O.search_bu(_score(lambda ts, te: 0.5, log), t_begin=0, t_end=24, k=1, s_min=8,
+                          s_max=16, delta_bu=4, h=1, t_max_idle=0, sigma=0.4, seed=5)
+    assert _spans(wins) == [(0, 7), (8, 15), (16, 23)], wins
+    assert log == [(0, 7), (0, 11), (4, 11), (8, 15), (8, 19), (12, 19), (16, 23)], log
+    assert n == 7
+
+
+def pin_bu_first_maximum():
+    # [0,11] and [4,11] both score 0.9, every other window 0.1; range [0, 40), s_min 8,
+    # s_max 16, delta 4, h = 1, T_maxIdle 0, sigma 0.5.  Ring N_1 of [0,7] lists [0,11]
+    # (a = 0) before [4,11] (a = 1): the climb moves to [0,11], where [4,11] ties and is not
+    # accepted.  The later climbs (starts 12, 20, 28) only see 0.1.
+    table = {(0, 11): 0.9, (4, 11): 0.9}
+    wins, _ = O.search_bu(_score(table, default=0.1), t_begin=0, t_end=40, k=1, s_min=8,
+                          s_max=16, delta_bu=4, h=1, t_max_idle=0, sigma=0.5, seed=5)
+    assert _spans(wins) == [(0, 11)], wins
+
+
+def pin_bu_restart_after_left_move():
+    # [6,13] scores 0.9, every other window 0.1; range [0, 24), s_min 8, s_max 16, delta 2,
+    # h = 1, T_maxIdle 0, sigma 0.5.
+    # Climb 0 at [0,7]: ring [0,9], [2,9]; nothing better, nothing kept; next start 8.
+    # Climb 1 at [8,15]: ring (a outer, b inner) [6,13], [6,15], [6,17], [8,17], [10,17];
+    # it moves left to [6,13], whose ring [4,11], [4,13], [4,15], [6,15], [8,15] is worse.
+    # [6,13] is kept and the next start is max(13 + 1, 8 + 8) = 16, not 14: climb 2 at
+    # [16,23] has ring [14,21], [14,23].
+    log = []
+    wins, _ = O.search_bu(_score({(6, 13): 0.9}, log, default=0.1), t_begin=0, t_end=24, k=1,
+                          s_min=8, s_max=16, delta_bu=2, h=1, t_max_idle=0, sigma=0.5, seed=5)
+    assert _spans(wins) == [(6, 13)], wins
+    assert log == [(0, 7), (0, 9), (2, 9),
+                   (8, 15), (6, 13), (6, 15), (6, 17), (8, 17), (10, 17),
+                   (4, 11), (4, 13), (4, 15), (6, 15), (8, 15),
+                   (16, 23), (14, 21), (14, 23)], log
+
+
+def _noise_table(ts, te):
+    # Windows of at least 8 points: 0.3 + 0.01 t_e - 0.1 |t_s - 4|, best at t_s = 4 and the
+    # longest window.  Shorter windows (the extension windows of 4 points): 0 for [0,3]
+    # (noise), 0.5 elsewhere.
+    if te - ts + 1 < 8:
+        return 0.0 if te < 4 else 0.5
+    return 0.3 + 0.01 * te - 0.1 * abs(ts - 4)
+
+
+def pin_bu_noise_drops_one_side():
+    # Range [0, 64), k = 1, s_min 8, s_max 24, delta 4, h = 1, T_maxIdle 0, p = 1, tau 0.1,
+    # sigma 0.5, pruning on.
+    # [0,7] (-0.03): best of the ring is [4,11] (0.41); the right extension [8,11] scores 0.5,
+    #   no noise.  Move.
+    # [4,11]: the left neighbour [0,11] (0.01) with extension [0,3] (0 < tau, 0.01 < 0.41,
+    #   I_w > 0) is noise: with p = 1 the left side is dropped.  Move to [4,15] (0.45).
+    # [4,15] -> [4,19] (0.49) -> [4,23] (0.53) -> [4,27] (0.57, 24 points): only neighbours
+    #   with a >= 0 are left, and those that extend the right end keep improving.
+    # At [4,27] no neighbour is better, so [4,27] (0.57 >= sigma) is kept; the next climb
+    #   starts at [28,35] and every later one scores below 0.  (Had the noise dropped both
+    #   sides, the first climb would have ended at [4,15] (0.45 < sigma) and the second would
+    #   have started at [16,23].)
+    log = []
+    wins, _ = O.search_bu(_score(_noise_table, log), t_begin=0, t_end=64, k=1, s_min=8,
+                          s_max=24, delta_bu=4, h=1, t_max_idle=0, p=1, tau=0.1, sigma=0.5,
+                          pruning=1, seed=5)
+    assert _spans(wins) == [(4, 27)], wins
+    assert abs(wins[0][2] - 0.57) < 1e-12, wins
+    assert (28, 35) in log and (16, 23) not in log, log
+
+
+SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip,
+               pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
+               pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side]

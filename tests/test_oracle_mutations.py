@@ -1,20 +1,23 @@
 """Planted mistakes in the oracle (CPU only): each must fail at least one pin.
 
-The oracle carries a switch that re-introduces one plausible mistake at a time (a dropped
-term, a strict instead of inclusive count, the point counted as its own neighbour,
-Kraskov's first estimator, a swapped dimension, the other tie-break, the Euclidean norm,
-the garbled entropy sign, psi(m - 1)).  With the switch on, the pins of
-``tests/_pins.py`` must notice.
+The oracle carries a switch that re-introduces one plausible mistake at a time.  In the
+estimator: a dropped term, a strict instead of inclusive count, the point counted as its own
+neighbour, Kraskov's first estimator, a swapped dimension, the other tie-break, the
+Euclidean norm, the garbled entropy sign, psi(m - 1).  In the searches: acceptance with >=,
+the last maximum of a ring winning, no s_min floor on the TD layer size, an extension window
+w_delta that overlaps w_o, Def. 6.2 without its I > 0 condition, the whole square instead of
+the ring N_r, and a noisy side dropping both sides.  With the switch on, the pins of
+``tests/_pins.py`` and ``tests/_search_pins.py`` must notice.
 """
 import pytest
 
 from oracle import oracle as O
-from tests import _pins
+from tests import _pins, _search_pins
 
 
 def _failures():
     failed = []
-    for pin in _pins.FAST_PINS:
+    for pin in _pins.FAST_PINS + _search_pins.SEARCH_PINS:
         try:
             pin()
         except AssertionError:

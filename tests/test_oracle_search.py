@@ -5,59 +5,14 @@ import pytest
 
 from oracle import oracle as O
 from paper_2204_09131_gb300 import synth
+from tests import _search_pins
 
 
-def _table_score(table, default=0.0, log=None):
-    def score(ts, te):
-        if log is not None:
-            log.append((ts, te))
-        v = table(ts, te) if callable(table) else table.get((ts, te), default)
-        return v, v
-    return score
-
-
-def test_td_layers_and_partitions_hand_traced():
-    # Correlated iff the window lies inside [20, 40).  Range [0, 48), s_max 16, s_min 8,
-    # k = 1 so delta = max(k+1, s_w/4) = 4 then 2.
-    # Layer 16: starts 0,4,8,12,16 uncorrelated, [20,35] correlated, next start 36 does
-    # not fit.  Layer 8: partitions [0,19] (starts 0..12 step 2) and [36,47] (36,38,40).
-    log = []
-    score = _table_score(lambda ts, te: 1.0 if ts >= 20 and te < 40 else 0.0, log=log)
-    wins, n = O.search_td(score, t_begin=0, t_end=48, k=1, s_min=8, s_max=16, sigma=0.5)
-    assert [(a, b) for a, b, _, _ in wins] == [(20, 35)]
-    assert n == 16 and len(log) == 16
-    assert log[:6] == [(t, t + 15) for t in (0, 4, 8, 12, 16, 20)]
-    assert log[6:] == [(t, t + 7) for t in range(0, 13, 2)] + [(36, 43), (38, 45), (40, 47)]
-
-
-def test_td_noise_skip_hand_traced():
-    # One layer of size 16, delta 4, p = 2, sigma 0.5, tau 0.1.  Windows [4,19] and
-    # [8,23] are each noise w.r.t. their overlap (I_delta < tau and I_w < I_o), so after
-    # the second detection the scan jumps to t_e + 1 = 24, where [24,39] is correlated.
-    table = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
-             (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.05, (24, 39): 0.6}
-    log = []
-    wins, n = O.search_td(_table_score(table, log=log), t_begin=0, t_end=48, k=1, s_min=16,
-                          s_max=16, delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
-    assert [(a, b) for a, b, _, _ in wins] == [(24, 39)]
-    assert log == [(0, 15), (4, 19), (4, 15), (16, 19), (8, 23), (8, 19), (20, 23), (24, 39)]
-    # Without pruning the scan shifts through 12, 16, 20 before reaching 24.
-    log2 = []
-    wins2, n2 = O.search_td(_table_score(table, log=log2), t_begin=0, t_end=48, k=1,
-                            s_min=16, s_max=16, delta_td=4, sigma=0.5, tau=0.1, p=2)
-    assert [(a, b) for a, b, _, _ in wins2] == [(24, 39)]
-    assert log2 == [(t, t + 15) for t in range(0, 25, 4)]
-
-
-def test_bu_climbs_to_single_peak():
-    # Score 1 - (|t_s - 20| + |t_e - 39|) / 100: a single peak at [20, 39].  From
-    # w0 = [0, 7] the climb moves both ends by delta = 4 until t_s = 20, then the end
-    # until 39, where every ring-1 neighbour is worse (T_maxIdle = 0 stops the climb).
-    score = _table_score(lambda ts, te: 1.0 - (abs(ts - 20) + abs(te - 39)) / 100.0)
-    wins, _ = O.search_bu(score, t_begin=0, t_end=100, k=1, s_min=8, s_max=40, delta_bu=4,
-                          h=1, t_max_idle=0, sigma=0.9, seed=3)
-    assert [(a, b) for a, b, _, _ in wins] == [(20, 39)]
-    assert wins[0][2] == pytest.approx(1.0)
+@pytest.mark.parametrize("pin", _search_pins.SEARCH_PINS, ids=lambda f: f.__name__)
+def test_hand_traced_search(pin):
+    """The hand traces of tests/_search_pins.py: which windows each search scores, in which
+    order, and what it returns, on mocked score tables."""
+    pin()
 
 
 def _check_properties(wins, n, s_min, s_max, sigma):
