@@ -37,10 +37,10 @@
  *
  * Pins: the estimator against the Sec. 7.1 example, hand-worked windows, independent
  * brute forces and closed forms; the searches against hand-traced score tables (layers,
- * partitions, noise skips, rings, acceptance, ties, restarts, one-sided pruning).
- * Parity unpinned: the LAHC history stream of SYCOS_BU beyond its SplitMix64 reference
- * outputs, the chunk semantics of Algorithm 4 and the deterministic runtime and sampling
- * of Algorithm 3; the paper gives no numbers or examples for them.
+ * partitions, noise skips, rings, acceptance, ties, restarts, one-sided pruning, the
+ * late-acceptance history).  Parity unpinned: the chunk semantics of Algorithm 4 and the
+ * deterministic runtime and sampling of Algorithm 3; the paper gives no numbers or
+ * examples for them.
  *
  * Build: gcc -O2 -fno-fast-math -ffp-contract=off -shared -fPIC (no flush-to-zero).
  */
@@ -79,7 +79,8 @@ enum {
     ORC_MUT_TD_DELTA_OVERLAP = 13, /* w_delta = [t_e0, t_e1], one point in w_o too */
     ORC_MUT_NOISE_NO_IO = 14,    /* Def. 6.2 without its I_w > 0 condition         */
     ORC_MUT_BU_SQUARE = 15,      /* evaluate the whole square, not the ring N_r    */
-    ORC_MUT_BU_DROP_BOTH = 16    /* a noisy side drops both sides' neighbours      */
+    ORC_MUT_BU_DROP_BOTH = 16,   /* a noisy side drops both sides' neighbours      */
+    ORC_MUT_NO_HISTORY = 17      /* plain hill climbing: accept only if > I_w      */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -596,6 +597,7 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
             int32_t v = (int32_t)(orc_splitmix64_at(p->seed, (climb << 32) + step + 1) % (uint64_t)h);
             int better = (bsc > L[v] || bsc > Iw);
             if (g_mutation == ORC_MUT_ACCEPT_GE) better = (bsc >= L[v] || bsc >= Iw);
+            if (g_mutation == ORC_MUT_NO_HISTORY) better = bsc > Iw;
             if (have_best && better) {
                 ws = bs; we = be; Iw = bsc; mw = bmi;
                 t_idle = 0;

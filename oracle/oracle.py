@@ -44,6 +44,7 @@ MUTATIONS = {
     "noise_no_io": 14,
     "bu_square": 15,
     "bu_drop_both": 16,
+    "no_history": 17,
 }
 
 

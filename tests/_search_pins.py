@@ -18,13 +18,16 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
 - ``pin_bu_restart_after_left_move``: a climb that ends left of its start does not move the
   next start back;
 - ``pin_bu_noise_drops_one_side``: a noisy extension drops only the neighbours that extend
-  that side.
+  that side;
+- ``pin_bu_late_acceptance``: the late-acceptance history of Algorithm 2 (h entries, the
+  step's index drawn from SplitMix64, the same entry compared and then updated).
 
 tests/test_oracle_mutations.py runs them against planted mistakes of the oracle's searches.
 """
 from __future__ import annotations
 
 from oracle import oracle as O
+from paper_2204_09131_gb300 import synth
 
 
 def _score(table, log=None, default=0.0):
@@ -185,6 +188,39 @@ def pin_bu_noise_drops_one_side():
     assert (28, 35) in log and (16, 23) not in log, log
 
 
+def _history_indices(seed, h, n):
+    # The history index of step s of climb 0: SplitMix64 output s + 1 of the seed, mod h
+    # (the generator module's own SplitMix64, pinned to reference outputs elsewhere).
+    return [int(z) % h for z in synth.splitmix64(seed, n, offset=0)]
+
+
+def pin_bu_late_acceptance():
+    # Late acceptance (Algorithm 2 with h = 2): a neighbour is taken when it beats the
+    # current window OR the history entry L[v] of this step, and L[v] is raised to the
+    # current score after the step.  Range [0, 40), s_min 8, s_max 16, delta 4, T_maxIdle 0,
+    # sigma 0.35.  Scores: [4,11] 0.5, [4,15] 0.3, [4,19] 0.9, [0,7] 0.1, the rest 0.05.
+    # Climb 0 from [0,7] (L = [0.1, 0.1]):
+    #   step 0, index v0: [4,11] (0.5) beats 0.1: move; L[v0] = 0.5.
+    #   step 1, index v1: the best of the ring of [4,11] is [4,15] (0.3), worse than 0.5.
+    #     v1 != v0: 0.3 > L[v1] = 0.1, so the worse window is taken; from there [4,19] (0.9)
+    #     is the best of the next ring, and [4,19] is kept.
+    #     v1 == v0: 0.3 < L[v0] = 0.5: the climb stops and [4,11] is kept.
+    # Later climbs start at 20 or 12 and only see 0.05.
+    table = {(4, 11): 0.5, (4, 15): 0.3, (4, 19): 0.9, (0, 7): 0.1}
+    kw = dict(t_begin=0, t_end=40, k=1, s_min=8, s_max=16, delta_bu=4, h=2, t_max_idle=0,
+              sigma=0.35)
+    seeds = {}
+    for seed in range(1, 64):
+        v = _history_indices(seed, 2, 2)
+        seeds.setdefault(v[0] != v[1], seed)
+    assert set(seeds) == {True, False}
+    wins, _ = O.search_bu(_score(table, default=0.05), seed=seeds[True], **kw)
+    assert _spans(wins) == [(4, 19)], wins
+    wins, _ = O.search_bu(_score(table, default=0.05), seed=seeds[False], **kw)
+    assert _spans(wins) == [(4, 11)], wins
+
+
 SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
-               pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side]
+               pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
+               pin_bu_late_acceptance]
