@@ -38,8 +38,8 @@
  * Pins: the estimator against the Sec. 7.1 example, hand-worked windows, independent
  * brute forces and closed forms; the searches against hand-traced score tables (layers,
  * partitions, noise skips, rings, acceptance, ties, restarts, one-sided pruning, the
- * late-acceptance history).  Parity unpinned: the chunk semantics of Algorithm 4 and the
- * deterministic runtime and sampling of Algorithm 3; the paper gives no numbers or
+ * late-acceptance history, the chunks of Algorithm 4).  Parity unpinned: the
+ * deterministic runtime and the sampling of Algorithm 3; the paper gives no numbers or
  * examples for them.
  *
  * Build: gcc -O2 -fno-fast-math -ffp-contract=off -shared -fPIC (no flush-to-zero).
@@ -80,7 +80,8 @@ enum {
     ORC_MUT_NOISE_NO_IO = 14,    /* Def. 6.2 without its I_w > 0 condition         */
     ORC_MUT_BU_SQUARE = 15,      /* evaluate the whole square, not the ring N_r    */
     ORC_MUT_BU_DROP_BOTH = 16,   /* a noisy side drops both sides' neighbours      */
-    ORC_MUT_NO_HISTORY = 17      /* plain hill climbing: accept only if > I_w      */
+    ORC_MUT_NO_HISTORY = 17,     /* plain hill climbing: accept only if > I_w      */
+    ORC_MUT_CHUNK_NO_OVERLAP = 18 /* Alg. 4 chunks [i, i + L) without the s_max lead */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -665,6 +666,7 @@ int orc_search_chunked(orc_score_fn f, void *user, int64_t t_begin, int64_t t_en
     if (!buf) return ORC_ENOMEM;
     for (int64_t i = 0; i < N && rc == ORC_OK; i += L) {
         int64_t a = t_begin + (i - p->s_max > 0 ? i - p->s_max : 0);
+        if (g_mutation == ORC_MUT_CHUNK_NO_OVERLAP) a = t_begin + i;
         int64_t b = t_begin + (i + L < N ? i + L : N);
         int64_t nw = 0, ne = 0;
         rc = (alg == 0 ? orc_search_td : orc_search_bu)(f, user, a, b, &q, buf, 65536, &nw, &ne);

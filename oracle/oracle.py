@@ -45,6 +45,7 @@ MUTATIONS = {
     "bu_square": 15,
     "bu_drop_both": 16,
     "no_history": 17,
+    "chunk_no_overlap": 18,
 }
 
 

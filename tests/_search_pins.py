@@ -20,7 +20,9 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
 - ``pin_bu_noise_drops_one_side``: a noisy extension drops only the neighbours that extend
   that side;
 - ``pin_bu_late_acceptance``: the late-acceptance history of Algorithm 2 (h entries, the
-  step's index drawn from SplitMix64, the same entry compared and then updated).
+  step's index drawn from SplitMix64, the same entry compared and then updated);
+- ``pin_chunks_overlap``: the chunks of Algorithm 4 reach s_max points back, and a window
+  found by two chunks is returned twice.
 
 tests/test_oracle_mutations.py runs them against planted mistakes of the oracle's searches.
 """
@@ -220,7 +222,20 @@ def pin_bu_late_acceptance():
     assert _spans(wins) == [(4, 11)], wins
 
 
+def pin_chunks_overlap():
+    # Algorithm 4 with n_p = 2 on [0, 64): L = 32, chunks [0, 32) and [32 - s_max, 64) =
+    # [16, 64).  One TD layer of 16 points (s_min = s_max = 16, k = 1, delta 4); only [16,31]
+    # is correlated.  Chunk 0 scores starts 0, 4, 8, 12, 16 and keeps [16,31]; chunk 1 keeps
+    # [16,31] at its first start, then scores 32, 36, 40, 44, 48.  Both copies are returned
+    # (11 windows scored).
+    log = []
+    wins, n = O.search_chunked(_score(lambda ts, te: 0.9 if (ts, te) == (16, 31) else 0.0, log),
+                               None, 0, 64, mode=0, chunks=2, k=1, s_min=16, s_max=16, sigma=0.5)
+    assert _spans(wins) == [(16, 31), (16, 31)], wins
+    assert n == 11 and log == [(t, t + 15) for t in (0, 4, 8, 12, 16, 16, 32, 36, 40, 44, 48)], (n, log)
+
+
 SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
-               pin_bu_late_acceptance]
+               pin_bu_late_acceptance, pin_chunks_overlap]
