@@ -38,9 +38,9 @@
  * Pins: the estimator against the Sec. 7.1 example, hand-worked windows, independent
  * brute forces and closed forms; the searches against hand-traced score tables (layers,
  * partitions, noise skips, rings, acceptance, ties, restarts, one-sided pruning, the
- * late-acceptance history, the chunks of Algorithm 4).  Parity unpinned: the
- * deterministic runtime and the sampling of Algorithm 3; the paper gives no numbers or
- * examples for them.
+ * late-acceptance history, the chunks of Algorithm 4, the pair-count runtime of
+ * Algorithm 3).  Parity unpinned: which partitions Algorithm 3 samples when it samples
+ * fewer than all of them (a seeded choice the paper leaves open).
  *
  * Build: gcc -O2 -fno-fast-math -ffp-contract=off -shared -fPIC (no flush-to-zero).
  */
@@ -81,7 +81,8 @@ enum {
     ORC_MUT_BU_SQUARE = 15,      /* evaluate the whole square, not the ring N_r    */
     ORC_MUT_BU_DROP_BOTH = 16,   /* a noisy side drops both sides' neighbours      */
     ORC_MUT_NO_HISTORY = 17,     /* plain hill climbing: accept only if > I_w      */
-    ORC_MUT_CHUNK_NO_OVERLAP = 18 /* Alg. 4 chunks [i, i + L) without the s_max lead */
+    ORC_MUT_CHUNK_NO_OVERLAP = 18, /* Alg. 4 chunks [i, i + L) without the s_max lead */
+    ORC_MUT_RUNTIME_WINDOWS = 19 /* Alg. 3 runtime = windows scored, not pairs     */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -732,7 +733,7 @@ static int orc_cost_score(void *user, int64_t t_s, int64_t t_e, double *score, d
 {
     orc_cost_scorer *c = (orc_cost_scorer *)user;
     double m = (double)(t_e - t_s + 1);
-    c->cost += m * (m - 1.0);
+    c->cost += g_mutation == ORC_MUT_RUNTIME_WINDOWS ? 1.0 : m * (m - 1.0);
     return c->f(c->user, t_s, t_e, score, mi);
 }
 

@@ -46,6 +46,7 @@ MUTATIONS = {
     "bu_drop_both": 16,
     "no_history": 17,
     "chunk_no_overlap": 18,
+    "runtime_windows": 19,
 }
 
 
@@ -362,22 +363,36 @@ def nscores(t_td, t_bu, nl_td, ns_bu, alpha=0.5):
     return a.value, b.value
 
 
-def search_auto(x, y, t_begin=0, t_end=None, partitions=20, samples=6, alpha=0.5, rho=0.5,
-                estimator=0, **kw):
+def search_auto(x_or_score, y=None, t_begin=0, t_end=None, partitions=20, samples=6, alpha=0.5,
+                rho=0.5, estimator=0, **kw):
     """Algorithm 3 (iSYCOS selection) over [t_begin, t_end); returns (windows, n_evals,
-    selected (0 TD / 1 BU), (nscore_TD, nscore_BU))."""
+    selected (0 TD / 1 BU), (nscore_TD, nscore_BU)).  Arguments as for :func:`search_td`."""
     params = make_params(**kw)
-    score = series_scorer(x, y, params.k, params.score_kind, estimator)
-    if t_end is None:
-        t_end = len(x)
+    if callable(x_or_score):
+        score = x_or_score
+
+        def cb(_user, ts, te, sc, mi):
+            try:
+                s, v = score(int(ts), int(te))
+            except Exception:
+                return -1
+            sc[0] = s
+            mi[0] = v
+            return 0
+        cfun = SCORE_FN(cb)
+        fptr, user_ref = ctypes.cast(cfun, ctypes.c_void_p), None
+    else:
+        fptr, user = series_scorer(x_or_score, y, params.k, params.score_kind, estimator)
+        user_ref = ctypes.byref(user)
+        if t_end is None:
+            t_end = len(x_or_score)
     sp = OrcSelectParams(partitions, samples, alpha, rho)
     cap = 1 << 16
     out = (OrcWindow * cap)()
     n_out, n_evals = ctypes.c_int64(), ctypes.c_int64()
     sel = ctypes.c_int32()
     sc = (ctypes.c_double * 2)()
-    fptr, user = score
-    rc = lib().orc_search_auto(fptr, ctypes.byref(user), t_begin, t_end, ctypes.byref(params),
+    rc = lib().orc_search_auto(fptr, user_ref, t_begin, t_end, ctypes.byref(params),
                                ctypes.byref(sp), out, cap, ctypes.byref(n_out), ctypes.byref(n_evals),
                                ctypes.byref(sel), sc)
     if rc != 0:

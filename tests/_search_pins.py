@@ -22,7 +22,10 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
 - ``pin_bu_late_acceptance``: the late-acceptance history of Algorithm 2 (h entries, the
   step's index drawn from SplitMix64, the same entry compared and then updated);
 - ``pin_chunks_overlap``: the chunks of Algorithm 4 reach s_max points back, and a window
-  found by two chunks is returned twice.
+  found by two chunks is returned twice;
+- ``pin_selection_runtime``: Algorithm 3's runtime of a search is the pair comparisons of
+  the windows it scores, averaged over the sampled partitions, and its window counts split
+  at rho * s_max.
 
 tests/test_oracle_mutations.py runs them against planted mistakes of the oracle's searches.
 """
@@ -235,7 +238,35 @@ def pin_chunks_overlap():
     assert n == 11 and log == [(t, t + 15) for t in (0, 4, 8, 12, 16, 16, 32, 36, 40, 44, 48)], (n, log)
 
 
+def pin_selection_runtime():
+    # Algorithm 3 with M = m = 2 partitions of [0, 64) (both sampled), alpha 0.5, rho 0.5;
+    # TD: s_min 8, s_max 16, k = 1 (deltas 4 and 2); BU: delta 4, h = 1, T_maxIdle 0.  The
+    # runtime of a search is the pair comparisons m (m - 1) of the windows it scores,
+    # averaged over the partitions.
+    # Nothing correlated, per partition of 32 points:
+    #   TD: 5 windows of 16 (starts 0..16) and 13 of 8 (starts 0..24): 5*240 + 13*56 = 1928.
+    #   BU: climbs at 0, 8, 16, 24 score 3, 6, 6 and 3 windows: [0,7] + [0,11], [4,11];
+    #     [8,15] + [4,11], [4,15], [4,19], [8,19], [12,19]; [16,23] + five likewise;
+    #     [24,31] + [20,27], [20,31]: 244 + 672 + 672 + 244 = 1832.
+    #   No window found: nscore_TD = 0.5 * 3760 / 1928, nscore_BU = 0.5 * 3760 / 1832; BU.
+    kw = dict(k=1, s_min=8, s_max=16, delta_bu=4, h=1, t_max_idle=0, sigma=0.5, seed=7)
+    wins, _, sel, sc = O.search_auto(_score(lambda ts, te: 0.0), None, 0, 64, partitions=2,
+                                     samples=2, alpha=0.5, rho=0.5, **kw)
+    assert wins == [] and sel == 1, (wins, sel)
+    assert abs(sc[0] - 0.5 * 3760 / 1928) < 1e-12 and abs(sc[1] - 0.5 * 3760 / 1832) < 1e-12, sc
+    # [0,15] correlated: in partition [0, 32) TD keeps it at its first window, then scores
+    # [16,31] and, in layer 8, the partition [16, 31] (starts 16..24): 2*240 + 5*56 = 760,
+    # one large window (16 > rho * s_max).  BU never scores [0,15] (it is not in a ring of
+    # its climbs) and costs 1832 as before.  t_TD = (760 + 1928) / 2 = 1344, t_BU = 1832:
+    # nscore_TD = 0.5 * 3176 / 1344 + 0.5 * 1, nscore_BU = 0.5 * 3176 / 1832 + 0; TD runs on
+    # the whole range and keeps [0,15].
+    wins, _, sel, sc = O.search_auto(_score(lambda ts, te: 0.9 if (ts, te) == (0, 15) else 0.0),
+                                     None, 0, 64, partitions=2, samples=2, alpha=0.5, rho=0.5, **kw)
+    assert _spans(wins) == [(0, 15)] and sel == 0, (wins, sel)
+    assert abs(sc[0] - (0.5 * 3176 / 1344 + 0.5)) < 1e-12 and abs(sc[1] - 0.5 * 3176 / 1832) < 1e-12, sc
+
+
 SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
-               pin_bu_late_acceptance, pin_chunks_overlap]
+               pin_bu_late_acceptance, pin_chunks_overlap, pin_selection_runtime]

@@ -7,7 +7,8 @@ Euclidean norm, the garbled entropy sign, psi(m - 1).  In the searches: acceptan
 the last maximum of a ring winning, no s_min floor on the TD layer size, an extension window
 w_delta that overlaps w_o, Def. 6.2 without its I > 0 condition, the whole square instead of
 the ring N_r, a noisy side dropping both sides, plain hill climbing without the
-late-acceptance history, and chunks without their s_max overlap.  With the switch on, the pins of
+late-acceptance history, chunks without their s_max overlap, and a selection runtime that
+counts windows instead of pair comparisons.  With the switch on, the pins of
 ``tests/_pins.py`` and ``tests/_search_pins.py`` must notice.
 """
 import pytest
