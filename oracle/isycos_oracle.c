@@ -82,7 +82,8 @@ enum {
     ORC_MUT_BU_DROP_BOTH = 16,   /* a noisy side drops both sides' neighbours      */
     ORC_MUT_NO_HISTORY = 17,     /* plain hill climbing: accept only if > I_w      */
     ORC_MUT_CHUNK_NO_OVERLAP = 18, /* Alg. 4 chunks [i, i + L) without the s_max lead */
-    ORC_MUT_RUNTIME_WINDOWS = 19 /* Alg. 3 runtime = windows scored, not pairs     */
+    ORC_MUT_RUNTIME_WINDOWS = 19, /* Alg. 3 runtime = windows scored, not pairs    */
+    ORC_MUT_TINY_TEST = 20       /* noise test on windows of fewer than k+1 points */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -471,7 +472,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                     int64_t o_s = t, o_e = t + s_w - delta - 1;
                     int64_t d_s = t + s_w - delta, d_e = t + s_w - 1;
                     if (g_mutation == ORC_MUT_TD_DELTA_OVERLAP) d_s -= 1;
-                    if (o_e - o_s + 1 >= p->k + 1 && d_e - d_s + 1 >= p->k + 1) {
+                    if ((o_e - o_s + 1 >= p->k + 1 && d_e - d_s + 1 >= p->k + 1) || g_mutation == ORC_MUT_TINY_TEST) {
                         double so, mo, sd, md;
                         rc = f(user, o_s, o_e, &so, &mo);
                         if (rc) break;
@@ -580,7 +581,7 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                     int64_t es = side == 0 ? ws - r * delta : we + 1;
                     int64_t ee = side == 0 ? ws - 1 : we + r * delta;
                     int noise = 0;
-                    if (ee - es + 1 >= p->k + 1) {
+                    if (ee - es + 1 >= p->k + 1 || g_mutation == ORC_MUT_TINY_TEST) {
                         double sd, md;
                         rc = f(user, es, ee, &sd, &md);
                         if (rc) break;

@@ -47,6 +47,7 @@ MUTATIONS = {
     "no_history": 17,
     "chunk_no_overlap": 18,
     "runtime_windows": 19,
+    "tiny_test": 20,
 }
 
 

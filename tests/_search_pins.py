@@ -9,7 +9,7 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
   uncorrelated partitions and the literal partition end of Algorithm 1;
 - ``pin_td_size_floor``: reduce(s_w) stops at s_min (a layer of s_min points, not s_w / 2);
 - ``pin_td_noise_skip``: w_o = [t_s1, t_e0], w_delta = [t_e0 + 1, t_e1] and the skip after p
-  detections (Def. 6.2 in SYCOS_TD);
+  detections (Def. 6.2 in SYCOS_TD); no test when w_delta has fewer than k + 1 points;
 - ``pin_td_noise_needs_positive_overlap``: Def. 6.2 only holds when I_{w_o} > 0;
 - ``pin_bu_single_peak``: a climb over a single-peak table;
 - ``pin_bu_plateau``: the ring N_1 (not the whole square), strict acceptance of Algorithm 2,
@@ -92,6 +92,13 @@ def pin_td_noise_skip():
                            delta_td=4, sigma=0.5, tau=0.1, p=2)
     assert _spans(wins2) == [(24, 39)], wins2
     assert log2 == [(t, t + 15) for t in range(0, 25, 4)], log2
+    # With k = 4 the extension w_delta of 4 points is below k + 1 and is never scored: no
+    # noise test runs, and the pruned scan is the unpruned one.
+    log3 = []
+    wins3, _ = O.search_td(_score(table, log3), t_begin=0, t_end=48, k=4, s_min=16, s_max=16,
+                           delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
+    assert _spans(wins3) == [(24, 39)], wins3
+    assert log3 == [(t, t + 15) for t in range(0, 25, 4)], log3
 
 
 def pin_td_noise_needs_positive_overlap():
