@@ -83,7 +83,8 @@ enum {
     ORC_MUT_NO_HISTORY = 17,     /* plain hill climbing: accept only if > I_w      */
     ORC_MUT_CHUNK_NO_OVERLAP = 18, /* Alg. 4 chunks [i, i + L) without the s_max lead */
     ORC_MUT_RUNTIME_WINDOWS = 19, /* Alg. 3 runtime = windows scored, not pairs    */
-    ORC_MUT_TINY_TEST = 20       /* noise test on windows of fewer than k+1 points */
+    ORC_MUT_TINY_TEST = 20,      /* noise test on windows of fewer than k+1 points */
+    ORC_MUT_RUN_NO_RESET = 21    /* TD: a window that is not noise keeps the count */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -483,7 +484,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                         noise = (so > 0.0 || g_mutation == ORC_MUT_NOISE_NO_IO) && (sd < p->tau) && (sc < so);
                     }
                 }
-                noise_run = noise ? noise_run + 1 : 0;
+                noise_run = noise ? noise_run + 1 : (g_mutation == ORC_MUT_RUN_NO_RESET ? noise_run : 0);
                 if (noise_run >= pcount) {
                     t = t + s_w;               /* skip the rest of the shifting (Sec. 6.2) */
                     noise_run = 0;

@@ -48,6 +48,7 @@ MUTATIONS = {
     "chunk_no_overlap": 18,
     "runtime_windows": 19,
     "tiny_test": 20,
+    "run_no_reset": 21,
 }
 
 

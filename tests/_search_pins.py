@@ -10,6 +10,7 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
 - ``pin_td_size_floor``: reduce(s_w) stops at s_min (a layer of s_min points, not s_w / 2);
 - ``pin_td_noise_skip``: w_o = [t_s1, t_e0], w_delta = [t_e0 + 1, t_e1] and the skip after p
   detections (Def. 6.2 in SYCOS_TD); no test when w_delta has fewer than k + 1 points;
+- ``pin_td_noise_run_resets``: only consecutive detections count toward p;
 - ``pin_td_noise_needs_positive_overlap``: Def. 6.2 only holds when I_{w_o} > 0;
 - ``pin_bu_single_peak``: a climb over a single-peak table;
 - ``pin_bu_plateau``: the ring N_1 (not the whole square), strict acceptance of Algorithm 2,
@@ -99,6 +100,21 @@ def pin_td_noise_skip():
                            delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
     assert _spans(wins3) == [(24, 39)], wins3
     assert log3 == [(t, t + 15) for t in range(0, 25, 4)], log3
+
+
+def pin_td_noise_run_resets():
+    # One layer of size 16, delta 4, p = 2, sigma 0.5, tau 0.1.  [4,19] is noise (as in
+    # pin_td_noise_skip), [8,23] is not (its w_delta [20,23] scores 0.5 >= tau), [12,27] is
+    # noise again: the detections are not consecutive, so the count restarts at [8,23] and
+    # the scan never skips; every other window scores 0 (w_o at 0: no noise).  Starts 0..32.
+    table = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
+             (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.5,
+             (12, 27): 0.1, (12, 23): 0.3, (24, 27): 0.05}
+    log = []
+    wins, _ = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
+                          delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
+    assert wins == [], wins
+    assert [w for w in log if w[1] - w[0] + 1 == 16] == [(t, t + 15) for t in range(0, 33, 4)], log
 
 
 def pin_td_noise_needs_positive_overlap():
@@ -273,7 +289,7 @@ def pin_selection_runtime():
     assert abs(sc[0] - (0.5 * 3176 / 1344 + 0.5)) < 1e-12 and abs(sc[1] - 0.5 * 3176 / 1832) < 1e-12, sc
 
 
-SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip,
+SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip, pin_td_noise_run_resets,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
                pin_bu_late_acceptance, pin_chunks_overlap, pin_selection_runtime]
