@@ -84,7 +84,8 @@ enum {
     ORC_MUT_CHUNK_NO_OVERLAP = 18, /* Alg. 4 chunks [i, i + L) without the s_max lead */
     ORC_MUT_RUNTIME_WINDOWS = 19, /* Alg. 3 runtime = windows scored, not pairs    */
     ORC_MUT_TINY_TEST = 20,      /* noise test on windows of fewer than k+1 points */
-    ORC_MUT_RUN_NO_RESET = 21    /* TD: a window that is not noise keeps the count */
+    ORC_MUT_RUN_NO_RESET = 21,   /* TD: a window that is not noise keeps the count */
+    ORC_MUT_BU_RUN_NO_RESET = 22 /* BU: a step that is not noise keeps the count   */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -590,7 +591,8 @@ int orc_search_bu(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                         /* Def. 6.2 with w = current window, w' = extension, w'' = neighbour. */
                         noise = (Iw > 0.0 || g_mutation == ORC_MUT_NOISE_NO_IO) && (sd < p->tau) && (ext_sc[side] < Iw);
                     }
-                    noise_run[side] = noise ? noise_run[side] + 1 : 0;
+                    noise_run[side] = noise ? noise_run[side] + 1
+                                            : (g_mutation == ORC_MUT_BU_RUN_NO_RESET ? noise_run[side] : 0);
                     if (noise_run[side] >= pcount) {
                         dropped[side] = 1;
                         if (g_mutation == ORC_MUT_BU_DROP_BOTH) dropped[1 - side] = 1;

@@ -49,6 +49,7 @@ MUTATIONS = {
     "runtime_windows": 19,
     "tiny_test": 20,
     "run_no_reset": 21,
+    "bu_run_no_reset": 22,
 }
 
 

@@ -20,6 +20,7 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
   next start back;
 - ``pin_bu_noise_drops_one_side``: a noisy extension drops only the neighbours that extend
   that side;
+- ``pin_bu_noise_run_resets``: each side's detections count toward p only while consecutive;
 - ``pin_bu_late_acceptance``: the late-acceptance history of Algorithm 2 (h entries, the
   step's index drawn from SplitMix64, the same entry compared and then updated);
 - ``pin_chunks_overlap``: the chunks of Algorithm 4 reach s_max points back, and a window
@@ -222,6 +223,34 @@ def _history_indices(seed, h, n):
     return [int(z) % h for z in synth.splitmix64(seed, n, offset=0)]
 
 
+def _shift_table(ts, te):
+    # W_j = [4j, 4j + 7] scores 0.1 + 0.1 j for j = 0..5, other windows of 8+ points 0; of the
+    # 4-point extension windows, [0,3] and [8,11] score 0 (noise) and the rest 0.5.
+    if te - ts + 1 < 8:
+        return 0.0 if (ts, te) in ((0, 3), (8, 11)) else 0.5
+    if te - ts == 7 and ts % 4 == 0 and ts <= 20:
+        return 0.1 + 0.1 * (ts // 4)
+    return 0.0
+
+
+def pin_bu_noise_run_resets():
+    # Range [0, 64), k = 1, s_min 8, s_max 16, delta 4, h = 1, T_maxIdle 0, p = 2, tau 0.1,
+    # sigma 0.5, pruning on.  The climb shifts right one delta per step, W_0 -> W_5: the ring of
+    # W_j is W_{j-1}, [4j-4, 4j+7], [4j-4, 4j+11], [4j, 4j+11] (all 0 or lower) and W_{j+1}.
+    # Left extension [4j-4, 4j-1] of W_j (its neighbour [4j-4, 4j+7] scores 0 < I_w):
+    #   j = 1: [0,3] noise (count 1); j = 2: [4,7] not noise (count 0); j = 3: [8,11] noise
+    #   (count 1 < p): the left side stays, and at W_4 = [16,23] the neighbour (a = -1, b = 1)
+    #   [12,27] is scored.
+    # Right extension [4j+8, 4j+11]: noise at j = 0 only ([8,11]), never twice in a row.
+    # At W_5 nothing is better: [20,27] (0.6) is kept.
+    log = []
+    wins, _ = O.search_bu(_score(_shift_table, log), t_begin=0, t_end=64, k=1, s_min=8,
+                          s_max=16, delta_bu=4, h=1, t_max_idle=0, p=2, tau=0.1, sigma=0.5,
+                          pruning=1, seed=5)
+    assert _spans(wins) == [(20, 27)], wins
+    assert (12, 27) in log, log
+
+
 def pin_bu_late_acceptance():
     # Late acceptance (Algorithm 2 with h = 2): a neighbour is taken when it beats the
     # current window OR the history entry L[v] of this step, and L[v] is raised to the
@@ -292,4 +321,5 @@ def pin_selection_runtime():
 SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip, pin_td_noise_run_resets,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
-               pin_bu_late_acceptance, pin_chunks_overlap, pin_selection_runtime]
+               pin_bu_noise_run_resets, pin_bu_late_acceptance, pin_chunks_overlap,
+               pin_selection_runtime]
