@@ -52,6 +52,16 @@ def _spans(wins):
     return [(a, b) for a, b, _, _ in wins]
 
 
+# Score tables of the traces below ((t_s, t_e) -> score; unlisted windows score 0).
+_NOISE_SKIP = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
+               (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.05, (24, 39): 0.6}
+_NOISE_RUN = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
+              (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.5,
+              (12, 27): 0.1, (12, 23): 0.3, (24, 27): 0.05}
+_NOISE_OVERLAP_ZERO = {(0, 15): 0.2, (4, 19): -0.1, (4, 15): 0.0, (16, 19): 0.05}
+_LATE = {(4, 11): 0.5, (4, 15): 0.3, (4, 19): 0.9, (0, 7): 0.1}
+
+
 def pin_td_layers():
     # Correlated iff the window lies inside [20, 40).  Range [0, 48), s_max 16, s_min 8,
     # k = 1 so delta = max(k+1, s_w/4) = 4 then 2.
@@ -81,8 +91,7 @@ def pin_td_noise_skip():
     # One layer of size 16, delta 4, p = 2, sigma 0.5, tau 0.1.  Windows [4,19] and
     # [8,23] are each noise w.r.t. their overlap (I_delta < tau and I_w < I_o), so after
     # the second detection the scan jumps to t_e + 1 = 24, where [24,39] is correlated.
-    table = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
-             (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.05, (24, 39): 0.6}
+    table = _NOISE_SKIP
     log = []
     wins, n = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
                           delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
@@ -108,9 +117,7 @@ def pin_td_noise_run_resets():
     # pin_td_noise_skip), [8,23] is not (its w_delta [20,23] scores 0.5 >= tau), [12,27] is
     # noise again: the detections are not consecutive, so the count restarts at [8,23] and
     # the scan never skips; every other window scores 0 (w_o at 0: no noise).  Starts 0..32.
-    table = {(0, 15): 0.2, (4, 19): 0.1, (4, 15): 0.3, (16, 19): 0.05,
-             (8, 23): 0.1, (8, 19): 0.3, (20, 23): 0.5,
-             (12, 27): 0.1, (12, 23): 0.3, (24, 27): 0.05}
+    table = _NOISE_RUN
     log = []
     wins, _ = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
                           delta_td=4, sigma=0.5, tau=0.1, p=2, pruning=1)
@@ -123,7 +130,7 @@ def pin_td_noise_needs_positive_overlap():
     # I_{w_o} = 0, Def. 6.2 does not hold even though I_delta = 0.05 < tau and I_w = -0.1 <
     # I_{w_o}, so the layer keeps shifting by 4 (every other window scores 0 and is never
     # noise) through the last start 32.
-    table = {(0, 15): 0.2, (4, 19): -0.1, (4, 15): 0.0, (16, 19): 0.05}
+    table = _NOISE_OVERLAP_ZERO
     log = []
     wins, _ = O.search_td(_score(table, log), t_begin=0, t_end=48, k=1, s_min=16, s_max=16,
                           delta_td=4, sigma=0.5, tau=0.1, p=1, pruning=1)
@@ -251,6 +258,16 @@ def pin_bu_noise_run_resets():
     assert (12, 27) in log, log
 
 
+def _late_seeds():
+    # the first seeds whose first two history indices (h = 2) differ (True) and coincide (False)
+    seeds = {}
+    for seed in range(1, 64):
+        v = _history_indices(seed, 2, 2)
+        seeds.setdefault(v[0] != v[1], seed)
+    assert set(seeds) == {True, False}
+    return seeds
+
+
 def pin_bu_late_acceptance():
     # Late acceptance (Algorithm 2 with h = 2): a neighbour is taken when it beats the
     # current window OR the history entry L[v] of this step, and L[v] is raised to the
@@ -263,17 +280,12 @@ def pin_bu_late_acceptance():
     #     is the best of the next ring, and [4,19] is kept.
     #     v1 == v0: 0.3 < L[v0] = 0.5: the climb stops and [4,11] is kept.
     # Later climbs start at 20 or 12 and only see 0.05.
-    table = {(4, 11): 0.5, (4, 15): 0.3, (4, 19): 0.9, (0, 7): 0.1}
     kw = dict(t_begin=0, t_end=40, k=1, s_min=8, s_max=16, delta_bu=4, h=2, t_max_idle=0,
               sigma=0.35)
-    seeds = {}
-    for seed in range(1, 64):
-        v = _history_indices(seed, 2, 2)
-        seeds.setdefault(v[0] != v[1], seed)
-    assert set(seeds) == {True, False}
-    wins, _ = O.search_bu(_score(table, default=0.05), seed=seeds[True], **kw)
+    seeds = _late_seeds()
+    wins, _ = O.search_bu(_score(_LATE, default=0.05), seed=seeds[True], **kw)
     assert _spans(wins) == [(4, 19)], wins
-    wins, _ = O.search_bu(_score(table, default=0.05), seed=seeds[False], **kw)
+    wins, _ = O.search_bu(_score(_LATE, default=0.05), seed=seeds[False], **kw)
     assert _spans(wins) == [(4, 11)], wins
 
 
@@ -323,3 +335,60 @@ SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip, pin_td_noise
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
                pin_bu_noise_run_resets, pin_bu_late_acceptance, pin_chunks_overlap,
                pin_selection_runtime]
+
+
+def _table(t, default=0.0):
+    return lambda ts, te: t.get((ts, te), default)
+
+
+def machine_cases():
+    """The traces above as (name, search, score, t_end, parameters, windows) for other
+    implementations of the searches: ``search`` is "td", "bu", "chunked" (parameters carry
+    mode and chunks) or "auto" (partitions, samples, alpha, rho); ``score`` maps (t_s, t_e)
+    to the window's score on [0, t_end); ``windows`` is the hand-traced result."""
+    td1 = dict(k=1, s_min=16, s_max=16, delta_td=4, sigma=0.5, tau=0.1, pruning=1)
+    bu1 = dict(k=1, s_min=8, s_max=16, delta_bu=4, h=1, t_max_idle=0, seed=5)
+    seeds = _late_seeds()
+    late = dict(k=1, s_min=8, s_max=16, delta_bu=4, h=2, t_max_idle=0, sigma=0.35)
+    sel = dict(k=1, s_min=8, s_max=16, delta_bu=4, h=1, t_max_idle=0, sigma=0.5, seed=7,
+               partitions=2, samples=2, alpha=0.5, rho=0.5)
+    return [
+        ("td_layers", "td", lambda ts, te: 1.0 if ts >= 20 and te < 40 else 0.0, 48,
+         dict(k=1, s_min=8, s_max=16, sigma=0.5), [(20, 35)]),
+        ("td_size_floor", "td", lambda ts, te: 0.0, 48, dict(k=1, s_min=16, s_max=24, sigma=0.5), []),
+        ("td_noise_skip", "td", _table(_NOISE_SKIP), 48, dict(td1, p=2), [(24, 39)]),
+        ("td_noise_tiny", "td", _table(_NOISE_SKIP), 48, dict(td1, p=2, k=4), [(24, 39)]),
+        ("td_noise_run_resets", "td", _table(_NOISE_RUN), 48, dict(td1, p=2), []),
+        ("td_noise_needs_positive_overlap", "td", _table(_NOISE_OVERLAP_ZERO), 48, dict(td1, p=1), []),
+        ("bu_single_peak", "bu", lambda ts, te: 1.0 - (abs(ts - 20) + abs(te - 39)) / 100.0, 100,
+         dict(bu1, s_max=40, sigma=0.9, seed=3), [(20, 39)]),
+        ("bu_plateau", "bu", lambda ts, te: 0.5, 24, dict(bu1, sigma=0.4), [(0, 7), (8, 15), (16, 23)]),
+        ("bu_first_maximum", "bu", _table({(0, 11): 0.9, (4, 11): 0.9}, 0.1), 40, dict(bu1, sigma=0.5),
+         [(0, 11)]),
+        ("bu_restart_after_left_move", "bu", _table({(6, 13): 0.9}, 0.1), 24,
+         dict(bu1, delta_bu=2, sigma=0.5), [(6, 13)]),
+        ("bu_noise_drops_one_side", "bu", _noise_table, 64,
+         dict(bu1, s_max=24, p=1, tau=0.1, sigma=0.5, pruning=1), [(4, 27)]),
+        ("bu_noise_run_resets", "bu", _shift_table, 64, dict(bu1, p=2, tau=0.1, sigma=0.5, pruning=1),
+         [(20, 27)]),
+        ("bu_late_acceptance_taken", "bu", _table(_LATE, 0.05), 40, dict(late, seed=seeds[True]), [(4, 19)]),
+        ("bu_late_acceptance_same_index", "bu", _table(_LATE, 0.05), 40, dict(late, seed=seeds[False]),
+         [(4, 11)]),
+        ("chunks_overlap", "chunked", lambda ts, te: 0.9 if (ts, te) == (16, 31) else 0.0, 64,
+         dict(mode=0, chunks=2, k=1, s_min=16, s_max=16, sigma=0.5), [(16, 31), (16, 31)]),
+        ("selection_nothing_found", "auto", lambda ts, te: 0.0, 64, sel, []),
+        ("selection_td", "auto", lambda ts, te: 0.9 if (ts, te) == (0, 15) else 0.0, 64, sel, [(0, 15)]),
+    ]
+
+
+def oracle_run(search, score, t_end, kw):
+    """The oracle's search on a machine case: (windows, evaluated-window count)."""
+    sc = _score(score)
+    if search == "td":
+        return O.search_td(sc, t_begin=0, t_end=t_end, **kw)
+    if search == "bu":
+        return O.search_bu(sc, t_begin=0, t_end=t_end, **kw)
+    if search == "chunked":
+        return O.search_chunked(sc, None, 0, t_end, **kw)
+    wins, n, _, _ = O.search_auto(sc, None, 0, t_end, **kw)
+    return wins, n

@@ -12,14 +12,19 @@
 //   keys: the isycos_params fields (k, score_kind, sigma, tau, s_min, s_max, delta_td,
 //         delta_bu, h, t_max_idle, p, mode, pruning, max_steps, seed, sel_partitions,
 //         sel_samples, sel_alpha, sel_rho, chunks, estimator), t_begin, t_end,
-//         spec (climbs asked ahead), incremental (0, 1, 2)
+//         spec (climbs asked ahead), incremental (0, 1, 2),
+//         table (a text file of "t_s t_e score" lines: every window then scores from it, MI and
+//         normalised score alike, instead of the oracle's estimator), table_default (the score
+//         of a window the table does not list, 0 by default)
 // output: per pair "M <pair> <found> <decided>" then "W <t_s> <t_e> <score> <mi>" lines.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "search.h"
@@ -40,11 +45,21 @@ namespace {
 std::vector<std::vector<float>> g_x, g_y;   // series by id: pair p has ids 2p (x), 2p + 1 (y)
 std::vector<isycos_mi_out> g_open;          // results of the open launch
 int64_t g_windows = 0, g_rounds = 0;
+bool g_use_table = false;                                   // scores from a table, not the estimator
+std::map<std::pair<int64_t, int64_t>, double> g_table;     // (t_s, t_e) -> score
+double g_table_default = 0.0;
 
 isycos_status score(int32_t xs, int32_t ys, int64_t start, int32_t m, int k, int est,
                     isycos_mi_out *o) {
     const std::vector<float> &x = g_x[(size_t)xs / 2], &y = g_y[(size_t)ys / 2];
     if (start < 0 || m < k + 1 || start + m > (int64_t)x.size()) return ISYCOS_E_INVAL;
+    if (g_use_table) {
+        auto it = g_table.find({start, start + m - 1});
+        const double v = it == g_table.end() ? g_table_default : it->second;
+        *o = isycos_mi_out{v, 1.0, v, 0, 0};
+        ++g_windows;
+        return ISYCOS_OK;
+    }
     orc_mi r;
     if (orc_ksg_window_est(x.data() + start, y.data() + start, m, k, est, nullptr, nullptr, nullptr,
                            nullptr, nullptr, nullptr, &r) != 0)
@@ -164,6 +179,16 @@ int main(int argc, char **argv) {
         else if (key == "t_end") t_end = atoll(v);
         else if (key == "spec") ctx->opt_spec_climbs = atoi(v);
         else if (key == "incremental") ctx->opt_incremental = atoi(v);
+        else if (key == "table_default") g_table_default = atof(v);
+        else if (key == "table") {
+            FILE *tf = fopen(v, "r");
+            if (!tf) return 2;
+            long long a, b;
+            double sc;
+            while (fscanf(tf, "%lld %lld %lf", &a, &b, &sc) == 3) g_table[{a, b}] = sc;
+            fclose(tf);
+            g_use_table = true;
+        }
         else {
             fprintf(stderr, "unknown key %s\n", key.c_str());
             return 2;

@@ -18,6 +18,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2204_09131_gb300 import synth
+from tests import _search_pins
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -159,6 +160,30 @@ def test_selection_matches_oracle(driver, tmp_path, pairs):
     for (x, y), g in zip(pairs, got):
         ref, n, _, _ = O.search_auto(x, y, partitions=8, samples=3, s_max=128, pruning=1)
         _same(g, ref, n)
+
+
+@pytest.mark.parametrize("case", _search_pins.machine_cases(), ids=lambda c: c[0])
+def test_machines_follow_the_hand_traces(driver, tmp_path, case):
+    """The library's search machines on the hand-traced score tables of tests/_search_pins.py
+    (every window of the range listed with its score): the hand-traced windows, and the
+    oracle's decided-window count."""
+    name, search, score, t_end, kw, expect = case
+    zeros = np.zeros(t_end, np.float32)
+    series = _series_file(tmp_path, [(zeros, zeros)])
+    table = os.path.join(str(tmp_path), "table.txt")
+    with open(table, "w") as f:
+        for ts in range(t_end):
+            for te in range(ts, t_end):
+                f.write("%d %d %.17g\n" % (ts, te, score(ts, te)))
+    args = dict(table=table, t_end=t_end)
+    rename = dict(partitions="sel_partitions", samples="sel_samples", alpha="sel_alpha", rho="sel_rho")
+    for key, v in kw.items():
+        args[rename.get(key, key)] = v
+    args.setdefault("mode", {"td": 0, "bu": 1, "auto": 2}.get(search, 0))
+    got = _run(driver, series, **args)[0]
+    assert [(a, b) for a, b, _, _ in got["found"]] == expect, (name, got["found"])
+    ref, n = _search_pins.oracle_run(search, score, t_end, kw)
+    _same(got, ref, n)
 
 
 def test_launch_layout_invariants():
