@@ -162,11 +162,12 @@ def test_selection_matches_oracle(driver, tmp_path, pairs):
         _same(g, ref, n)
 
 
+@pytest.mark.parametrize("spec", [0, 24, 64])
 @pytest.mark.parametrize("case", _search_pins.machine_cases(), ids=lambda c: c[0])
-def test_machines_follow_the_hand_traces(driver, tmp_path, case):
+def test_machines_follow_the_hand_traces(driver, tmp_path, case, spec):
     """The library's search machines on the hand-traced score tables of tests/_search_pins.py
-    (every window of the range listed with its score): the hand-traced windows, and the
-    oracle's decided-window count."""
+    (every window of the range listed with its score), with 0, 24 and 64 BU climbs asked
+    ahead: the hand-traced windows, and the oracle's decided-window count."""
     name, search, score, t_end, kw, expect = case
     zeros = np.zeros(t_end, np.float32)
     series = _series_file(tmp_path, [(zeros, zeros)])
@@ -175,7 +176,7 @@ def test_machines_follow_the_hand_traces(driver, tmp_path, case):
         for ts in range(t_end):
             for te in range(ts, t_end):
                 f.write("%d %d %.17g\n" % (ts, te, score(ts, te)))
-    args = dict(table=table, t_end=t_end)
+    args = dict(table=table, t_end=t_end, spec=spec)
     rename = dict(partitions="sel_partitions", samples="sel_samples", alpha="sel_alpha", rho="sel_rho")
     for key, v in kw.items():
         args[rename.get(key, key)] = v
