@@ -162,13 +162,9 @@ def test_selection_matches_oracle(driver, tmp_path, pairs):
         _same(g, ref, n)
 
 
-@pytest.mark.parametrize("spec", [0, 24, 64])
-@pytest.mark.parametrize("case", _search_pins.machine_cases(), ids=lambda c: c[0])
-def test_machines_follow_the_hand_traces(driver, tmp_path, case, spec):
-    """The library's search machines on the hand-traced score tables of tests/_search_pins.py
-    (every window of the range listed with its score), with 0, 24 and 64 BU climbs asked
-    ahead: the hand-traced windows, and the oracle's decided-window count."""
-    name, search, score, t_end, kw, expect = case
+def _table_case(tmp_path, case, spec):
+    """The series file (zeros) and harness arguments of a hand-traced case in table mode."""
+    _, search, score, t_end, kw, _ = case
     zeros = np.zeros(t_end, np.float32)
     series = _series_file(tmp_path, [(zeros, zeros)])
     table = os.path.join(str(tmp_path), "table.txt")
@@ -181,6 +177,17 @@ def test_machines_follow_the_hand_traces(driver, tmp_path, case, spec):
     for key, v in kw.items():
         args[rename.get(key, key)] = v
     args.setdefault("mode", {"td": 0, "bu": 1, "auto": 2}.get(search, 0))
+    return series, args
+
+
+@pytest.mark.parametrize("spec", [0, 24, 64])
+@pytest.mark.parametrize("case", _search_pins.machine_cases(), ids=lambda c: c[0])
+def test_machines_follow_the_hand_traces(driver, tmp_path, case, spec):
+    """The library's search machines on the hand-traced score tables of tests/_search_pins.py
+    (every window of the range listed with its score), with 0, 24 and 64 BU climbs asked
+    ahead: the hand-traced windows, and the oracle's decided-window count."""
+    name, search, score, t_end, kw, expect = case
+    series, args = _table_case(tmp_path, case, spec)
     got = _run(driver, series, **args)[0]
     assert [(a, b) for a, b, _, _ in got["found"]] == expect, (name, got["found"])
     ref, n = _search_pins.oracle_run(search, score, t_end, kw)
@@ -411,3 +418,12 @@ def test_search_machines_memory_safe(tmp_path, pairs):
         out = subprocess.run(args, capture_output=True, text=True, timeout=900)
         assert "AddressSanitizer" not in out.stderr and "runtime error" not in out.stderr, out.stderr[-3000:]
         assert out.returncode == 0, (kw, out.stderr[-2000:])
+    # two hand-traced cases in table mode: BU with pruning and 64 climbs ahead, the selection
+    for case in _search_pins.machine_cases():
+        if case[0] not in ("bu_noise_run_resets", "selection_td"):
+            continue
+        series, kw = _table_case(tmp_path, case, 64)
+        out = subprocess.run([exe, series] + ["%s=%s" % kv for kv in kw.items()], capture_output=True,
+                             text=True, timeout=900)
+        assert "AddressSanitizer" not in out.stderr and "runtime error" not in out.stderr, out.stderr[-3000:]
+        assert out.returncode == 0, (case[0], out.stderr[-2000:])
