@@ -85,7 +85,8 @@ enum {
     ORC_MUT_RUNTIME_WINDOWS = 19, /* Alg. 3 runtime = windows scored, not pairs    */
     ORC_MUT_TINY_TEST = 20,      /* noise test on windows of fewer than k+1 points */
     ORC_MUT_RUN_NO_RESET = 21,   /* TD: a window that is not noise keeps the count */
-    ORC_MUT_BU_RUN_NO_RESET = 22 /* BU: a step that is not noise keeps the count   */
+    ORC_MUT_BU_RUN_NO_RESET = 22, /* BU: a step that is not noise keeps the count  */
+    ORC_MUT_TD_TAIL = 23         /* TD: also score a window ending at the partition end */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -455,11 +456,13 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
             int64_t t = a;
             int shifted = 0;     /* the current window is the previous one moved by delta */
             int noise_run = 0;
+            int64_t last_start = a - 1;    /* start of the last window scored (for a mutation) */
             while (t + s_w - 1 <= b) {
                 double sc, mi;
                 rc = f(user, t, t + s_w - 1, &sc, &mi);
                 if (rc) break;
                 ++evals;
+                last_start = t;
                 if (sc >= p->sigma) {
                     rc = orc_push(&S, t, t + s_w - 1, sc, mi);
                     if (rc) break;
@@ -494,6 +497,12 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                     t = t + delta;
                     shifted = 1;
                 }
+            }
+            if (g_mutation == ORC_MUT_TD_TAIL && rc == ORC_OK && b - s_w + 1 >= a &&
+                b - s_w + 1 > last_start) {
+                double sc, mi;
+                rc = f(user, b - s_w + 1, b, &sc, &mi);
+                if (rc == ORC_OK) ++evals;
             }
         }
         free(pa);

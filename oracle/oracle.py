@@ -50,6 +50,7 @@ MUTATIONS = {
     "tiny_test": 20,
     "run_no_reset": 21,
     "bu_run_no_reset": 22,
+    "td_tail": 23,
 }
 
 

@@ -9,8 +9,8 @@ w_delta that overlaps w_o, Def. 6.2 without its I > 0 condition, the whole squar
 the ring N_r, a noisy side dropping both sides, plain hill climbing without the
 late-acceptance history, chunks without their s_max overlap, and a selection runtime that
 counts windows instead of pair comparisons, a noise test on extensions of fewer than
-k + 1 points, and a detection count that is not reset by a TD window or a BU step that is
-not noise.  With the switch on, the pins of
+k + 1 points, a detection count that is not reset by a TD window or a BU step that is
+not noise, and a TD layer that also scores a window ending at its partition's end.  With the switch on, the pins of
 ``tests/_pins.py`` and ``tests/_search_pins.py`` must notice.
 """
 import pytest
