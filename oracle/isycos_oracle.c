@@ -86,7 +86,10 @@ enum {
     ORC_MUT_TINY_TEST = 20,      /* noise test on windows of fewer than k+1 points */
     ORC_MUT_RUN_NO_RESET = 21,   /* TD: a window that is not noise keeps the count */
     ORC_MUT_BU_RUN_NO_RESET = 22, /* BU: a step that is not noise keeps the count  */
-    ORC_MUT_TD_TAIL = 23         /* TD: also score a window ending at the partition end */
+    ORC_MUT_TD_TAIL = 23,        /* TD: also score (and keep, if correlated) a window
+                                    ending at the partition end                     */
+    ORC_MUT_SAMPLE_DRAW = 24     /* Alg. 3: sampling draws outputs 0 .. m-1 of the
+                                    stream instead of 1 .. m                        */
 };
 static int g_mutation = ORC_MUT_NONE;
 
@@ -503,6 +506,7 @@ int orc_search_td(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
                 double sc, mi;
                 rc = f(user, b - s_w + 1, b, &sc, &mi);
                 if (rc == ORC_OK) ++evals;
+                if (rc == ORC_OK && sc >= p->sigma) rc = orc_push(&S, b - s_w + 1, b, sc, mi);
             }
         }
         free(pa);
@@ -780,7 +784,8 @@ int orc_search_auto(orc_score_fn f, void *user, int64_t t_begin, int64_t t_end,
     /* Random sampling: partial Fisher-Yates shuffle driven by SplitMix64 outputs of the stream
      * seed ^ 0x5E1EC7 (one draw per sampled partition). */
     for (int32_t i = 0; i < ms; ++i) {
-        uint64_t r = orc_splitmix64_at(p->seed ^ 0x5E1EC7ULL, (uint64_t)i + 1);
+        uint64_t r = orc_splitmix64_at(p->seed ^ 0x5E1EC7ULL,
+                                       (uint64_t)i + (g_mutation == ORC_MUT_SAMPLE_DRAW ? 0 : 1));
         int32_t j = i + (int32_t)(r % (uint64_t)(M - i));
         int32_t t = idx[i]; idx[i] = idx[j]; idx[j] = t;
     }

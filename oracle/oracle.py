@@ -51,6 +51,7 @@ MUTATIONS = {
     "run_no_reset": 21,
     "bu_run_no_reset": 22,
     "td_tail": 23,
+    "sample_draw": 24,
 }
 
 

@@ -7,6 +7,8 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
 
 - ``pin_td_layers``: layer sizes s_max, s_max / 2, ..., the step delta = max(k + 1, s_w / 4),
   uncorrelated partitions and the literal partition end of Algorithm 1;
+- ``pin_td_tail_not_scored``: a layer stops at the last grid window that fits its partition;
+  a window ending at the partition end off that grid is never scored;
 - ``pin_td_size_floor``: reduce(s_w) stops at s_min (a layer of s_min points, not s_w / 2);
 - ``pin_td_noise_skip``: w_o = [t_s1, t_e0], w_delta = [t_e0 + 1, t_e1] and the skip after p
   detections (Def. 6.2 in SYCOS_TD); no test when w_delta has fewer than k + 1 points;
@@ -25,6 +27,9 @@ what comes out.  Each ``pin_*`` raises AssertionError when the oracle disagrees:
   step's index drawn from SplitMix64, the same entry compared and then updated);
 - ``pin_chunks_overlap``: the chunks of Algorithm 4 reach s_max points back, and a window
   found by two chunks is returned twice;
+- ``pin_selection_sampling``: which partitions Algorithm 3 samples for a seed, M and m (the
+  partial Fisher-Yates shuffle over SplitMix64 outputs 1 .. m), traced by hand from the
+  generator's published reference outputs, and that the sample decides the selection;
 - ``pin_selection_runtime``: Algorithm 3's runtime of a search is the pair comparisons of
   the windows it scores, averaged over the sampled partitions, and its window counts split
   at rho * s_max.
@@ -74,6 +79,19 @@ def pin_td_layers():
     assert n == 16 and len(log) == 16, (n, log)
     assert log[:6] == [(t, t + 15) for t in (0, 4, 8, 12, 16, 20)], log
     assert log[6:] == [(t, t + 7) for t in range(0, 13, 2)] + [(36, 43), (38, 45), (40, 47)], log
+
+
+def pin_td_tail_not_scored():
+    # One layer of 16 points (s_min = s_max = 16), k = 1, delta 4, range [0, 50).  The scan
+    # takes starts 0, 4, ..., 32; start 36 would end at 51 > 49, so the layer stops (Alg. 1
+    # loops while the window ends inside its partition).  The window [34, 49] that would end
+    # exactly at the partition end is not on that grid and is never scored, although the
+    # table makes it the only correlated window.
+    log = []
+    wins, n = O.search_td(_score(lambda ts, te: 0.9 if ts == 34 and te == 49 else 0.0, log),
+                          t_begin=0, t_end=50, k=1, s_min=16, s_max=16, sigma=0.5)
+    assert wins == [] and n == 9, (wins, n)
+    assert log == [(t, t + 15) for t in range(0, 33, 4)], log
 
 
 def pin_td_size_floor():
@@ -330,7 +348,48 @@ def pin_selection_runtime():
     assert abs(sc[0] - (0.5 * 3176 / 1344 + 0.5)) < 1e-12 and abs(sc[1] - 0.5 * 3176 / 1832) < 1e-12, sc
 
 
-SEARCH_PINS = [pin_td_layers, pin_td_size_floor, pin_td_noise_skip, pin_td_noise_run_resets,
+def pin_selection_sampling():
+    # Algorithm 3's random sampling (Sec. 5.3) as read here: m of M partitions chosen by a
+    # partial Fisher-Yates shuffle of 0 .. M-1 whose i-th swap (i = 0 .. m-1) takes position
+    # i + (r_(i+1) mod (M - i)), r_n the n-th SplitMix64 output of the stream seed ^ 0x5E1EC7.
+    # seed = 1234567 ^ 0x5E1EC7 = 5032000 makes that stream the one with state 1234567,
+    # whose first outputs are Vigna's reference values r_1 = 6457827717110365317 and
+    # r_2 = 3203168211198807973.  With M = 10, m = 2, by hand:
+    #   r_1 mod 10 = 7 (its last digit): swap positions 0 and 7 -> partition 7 first;
+    #   r_2 mod 9 = 7 (its digit sum 79 = 8 * 9 + 7): swap positions 1 and 1 + 7 = 8 ->
+    #   partition 8 second.
+    # On [0, 320) the partitions have L = 32 points, so the sample is [224, 256) then
+    # [256, 288), each searched by SYCOS_TD and then SYCOS_BU, before the selected search
+    # runs on the whole range from 0.
+    seed = 1234567 ^ 0x5E1EC7
+    assert seed == 5032000
+    kw = dict(k=1, s_min=8, s_max=16, delta_bu=4, h=1, t_max_idle=0, sigma=0.5, seed=seed)
+    log = []
+    O.search_auto(_score(lambda ts, te: 0.0, log), None, 0, 320, partitions=10, samples=2,
+                  alpha=0.5, rho=0.5, **kw)
+    parts = []
+    for ts, te in log:
+        q = ts // 32
+        if not parts or parts[-1] != q:
+            parts.append(q)
+    assert parts[:3] == [7, 8, 0], parts[:3]
+    # the sampled searches stay inside their partitions: TD then BU on [224, 256), then on
+    # [256, 288)
+    n_sample = next(i for i, (ts, _) in enumerate(log) if ts < 224)
+    assert n_sample > 0 and all(224 <= ts and te < 32 * (ts // 32 + 1) for ts, te in log[:n_sample])
+    # The sample decides the choice: [224, 239] (16 points, large: > rho s_max = 8) is the
+    # only correlated window.  TD finds it in partition 7, BU (windows of 8..12 points
+    # around its climbs, all scoring 0) does not, so nl_TD = 1, ns_BU = 0 and nscore_TD =
+    # 0.5 / rt_TD + 0.5 > nscore_BU = 0.5 / rt_BU (both rt near 1/2): SYCOS_TD runs on the
+    # whole range and returns the window.  A sample without partition 7 finds nothing, and
+    # the cheaper BU would run and miss it.
+    wins, _, sel, _ = O.search_auto(_score(lambda ts, te: 0.9 if (ts, te) == (224, 239) else 0.0),
+                                    None, 0, 320, partitions=10, samples=2, alpha=0.5, rho=0.5, **kw)
+    assert sel == 0 and _spans(wins) == [(224, 239)], (sel, wins)
+
+
+SEARCH_PINS = [pin_td_layers, pin_td_tail_not_scored, pin_selection_sampling, pin_td_size_floor,
+               pin_td_noise_skip, pin_td_noise_run_resets,
                pin_td_noise_needs_positive_overlap, pin_bu_single_peak, pin_bu_plateau,
                pin_bu_first_maximum, pin_bu_restart_after_left_move, pin_bu_noise_drops_one_side,
                pin_bu_noise_run_resets, pin_bu_late_acceptance, pin_chunks_overlap,
@@ -378,6 +437,11 @@ def machine_cases():
          dict(mode=0, chunks=2, k=1, s_min=16, s_max=16, sigma=0.5), [(16, 31), (16, 31)]),
         ("selection_nothing_found", "auto", lambda ts, te: 0.0, 64, sel, []),
         ("selection_td", "auto", lambda ts, te: 0.9 if (ts, te) == (0, 15) else 0.0, 64, sel, [(0, 15)]),
+        ("selection_sampled_partitions", "auto",
+         lambda ts, te: 0.9 if (ts, te) == (224, 239) else 0.0, 320,
+         dict(sel, seed=1234567 ^ 0x5E1EC7, partitions=10), [(224, 239)]),
+        ("td_tail_not_scored", "td", lambda ts, te: 0.9 if (ts, te) == (34, 49) else 0.0, 50,
+         dict(k=1, s_min=16, s_max=16, sigma=0.5), []),
     ]
 
 

@@ -10,7 +10,9 @@ the ring N_r, a noisy side dropping both sides, plain hill climbing without the
 late-acceptance history, chunks without their s_max overlap, and a selection runtime that
 counts windows instead of pair comparisons, a noise test on extensions of fewer than
 k + 1 points, a detection count that is not reset by a TD window or a BU step that is
-not noise, and a TD layer that also scores a window ending at its partition's end.  With the switch on, the pins of
+not noise, a TD layer that also scores (and keeps) a window ending at its partition's end,
+and a selection sample drawn from the generator's outputs 0 .. m-1 instead of 1 .. m.  With
+the switch on, the pins of
 ``tests/_pins.py`` and ``tests/_search_pins.py`` must notice.
 """
 import pytest
