@@ -360,8 +360,12 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
  * holds them until the process exits.  The first call on a device (with that device
  * current) resolves the array's address with cudaGetSymbolAddress and uploads the tables,
  * so it should come before any stream capture.  Calls share the array, which keeps the last
- * call's contents: calls that overlap on the GPU race.  Asynchronous on cuda_stream;
- * windows outside [0, n) or with m < k + 1 or m > max_m get NaN results.
+ * call's contents: calls that overlap on the GPU race.  Every window takes the brute-force
+ * MI path (the sorted path's work memory would not fit a static array of modest size), so
+ * windows above about 1,000 points run slower than through a context that chose the sorted
+ * path; results are the same.  Asynchronous on cuda_stream: windows outside [0, n) or with
+ * m < k + 1 or m > max_m get NaN mi, h_w and nmi and zero sums, which is the only report of
+ * them (the call reads nothing back from the device).
  * Errors: E_INVAL (k, max_m, NULL pointers, or n_w > ISYCOS_NOALLOC_MAX_WINDOWS, the size
  * of the static scratch), E_CUDA. */
 #define ISYCOS_NOALLOC_MAX_WINDOWS 65536

@@ -88,6 +88,11 @@ struct PrepArgs {
     isycos_mi_out *out;              // invalid windows get NaN results
 };
 
+// The 2^-32 fixed-point digamma and log tables, entries 0 .. kTableN - 1 (runtime.cu):
+// psi_fx[n] = round(psi(n) 2^32) by the binary64 forward recurrence from psi(1) = -gamma,
+// log_fx[n] = round(ln(n) 2^32); entry 0 of both is 0.
+void fill_fixed_tables(long long *psi_fx, long long *log_fx);
+
 // Launchers (kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(int k, int nt, size_t smem, int *blocks_per_sm);

@@ -16,7 +16,6 @@
 // before any stream capture.  All calls share the array and it keeps the last call's
 // contents, so calls that overlap on the GPU (different streams, or host threads) race;
 // every call clears the counters it needs before use.
-#include <math.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -89,8 +88,7 @@ __global__ void noalloc_classify(NoallocPrep a) {
     const int32_t m = a.sizes[i];
     const bool ok = m >= a.k + 1 && m <= a.max_m && s >= 0 && s + m <= a.n;
     if (!ok) {
-        ctl_slot(a.scratch)[i] = -1;
-        atomicOr(ctl_counts(a.scratch) + kBuckets + 3, 1);
+        ctl_slot(a.scratch)[i] = -1;   // invalid: its NaN result is the only report
         const double nan = __longlong_as_double(0x7ff8000000000000ll);
         a.out[i].mi = nan;
         a.out[i].h_w = nan;
@@ -124,19 +122,10 @@ __global__ void noalloc_scatter(NoallocPrep a) {
     ctl_items(a.scratch)[ctl_table(a.scratch)->item_off[q] + ctl_pos(a.scratch)[i]] = it;
 }
 
-// Digamma by the forward recurrence psi(n + 1) = psi(n) + 1/n from psi(1) = -gamma, and
-// ln n, both rounded to 2^-32 (the tables the batched kernel reads).
+// The tables the batched kernel reads, built by the same routine as a context's.
 void build_host_tables() {
     if (h_tables_built) return;
-    const double gamma = 0.57721566490153286060651209008240243;
-    double psi = -gamma;
-    h_psi_fx[0] = 0;
-    h_log_fx[0] = 0;
-    for (int n = 1; n < kTableN; ++n) {
-        h_psi_fx[n] = llround(ldexp(psi, 32));
-        h_log_fx[n] = llround(ldexp(log((double)n), 32));
-        psi = psi + 1.0 / (double)n;
-    }
+    fill_fixed_tables(h_psi_fx, h_log_fx);
     h_tables_built = true;
 }
 
@@ -206,7 +195,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     pa.nt = nt;
     pa.scratch = d.scratch;
     pa.out = d_out;
-    // bucket counters, the three work counters and the error flag start at zero on every call
+    // bucket counters and the three work counters start at zero on every call
     if (cudaMemsetAsync(d.scratch, 0, 128, st) != cudaSuccess) return ISYCOS_E_CUDA;
     const int blocks = (int)((n_w + 255) / 256);
     noalloc_classify<<<blocks, 256, 0, st>>>(pa);

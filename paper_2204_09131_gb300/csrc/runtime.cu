@@ -410,18 +410,24 @@ static isycos_status sync_series_table(isycos_ctx *ctx, cudaStream_t st) {
     return ISYCOS_OK;
 }
 
-static void build_tables(std::vector<long long> &psi_fx, std::vector<long long> &log_fx) {
+void fill_fixed_tables(long long *psi_fx, long long *log_fx) {
     // psi(1) = -gamma, psi(n + 1) = psi(n) + 1/n (binary64 forward recurrence); values
     // rounded to the nearest multiple of 2^-32.
     const double gamma = 0.57721566490153286060651209008240243;
-    psi_fx.assign(kTableN, 0);
-    log_fx.assign(kTableN, 0);
+    psi_fx[0] = 0;
+    log_fx[0] = 0;
     double psi = -gamma;
     for (int n = 1; n < kTableN; ++n) {
         psi_fx[n] = llround(ldexp(psi, 32));
         log_fx[n] = llround(ldexp(log((double)n), 32));
         psi = psi + 1.0 / (double)n;
     }
+}
+
+static void build_tables(std::vector<long long> &psi_fx, std::vector<long long> &log_fx) {
+    psi_fx.assign(kTableN, 0);
+    log_fx.assign(kTableN, 0);
+    fill_fixed_tables(psi_fx.data(), log_fx.data());
 }
 
 }  // namespace isy

@@ -158,6 +158,14 @@ def planted_pair(cfg: int, pair: int, n: int, coverage: float = 0.3, len_lo: int
     return x.astype(np.float32), y.astype(np.float32), segs
 
 
+def tied_pair(pair: int, n: int, cfg: int = 5):
+    """A tie-heavy pair: both series of :func:`planted_pair` with planted multi-scale
+    relations of 100..50,000 samples, quantised to 0.1 steps (many equal values, equal
+    distances and duplicate points).  Returns float32 (x, y, segments)."""
+    x, y, segs = planted_pair(cfg, pair, n, len_lo=100, len_hi=min(50000, max(100, n // 2)))
+    return quantize(x), quantize(y), segs
+
+
 def _mixed_noise(seed: int, n: int) -> np.ndarray:
     """Independent noise in segments of 100..10000 samples, each from a family drawn
     from {gaussian, uniform, laplace} (unit variance)."""

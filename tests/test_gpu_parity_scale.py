@@ -1,0 +1,254 @@
+"""Parity with the oracle at the benchmark's settings and on tie-heavy data (GPU).
+
+- SYCOS_TD and SYCOS_BU (Algorithms 1 and 2 with the Sec. 6 pruning) on 40,000-point
+  prefixes of the 64 x 100k benchmark pairs, k = 4, window sizes 32..4096, run as the
+  benchmark runs them (one isycos_search_queries call, autotuned MI paths, incremental
+  chains on), and again with each MI path and chain setting forced: windows identical to
+  the oracle's, scores within 1e-12, decided-window counts equal to its evaluation counts.
+- 0.1-quantised pairs (equal values, equal distances and duplicate points everywhere),
+  k = 3 and 6, more than 2,000 windows stratified over every size bucket up to 16,384
+  points: S_psi and S_log bit-exact against the oracle up to 4,096 points, per-point
+  (n_x, n_y, c) bit-exact on sampled points above that.
+- Mixed-noise pairs (70 % independent Gaussian / uniform / Laplace noise, 30 % planted
+  segments of 100..10,000 samples): TD and BU with pruning on and off, each against the
+  oracle in the same mode.
+- Served queries (continuous batching) against the oracle's searches.
+The oracle runs in a spawned process pool; its expected values never come from the GPU.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from tests import _oracle_jobs as J
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+PREFIX = 40000
+BENCH_PARAMS = dict(k=4, s_min=32, s_max=4096, sigma=0.2, tau=0.05, pruning=1, seed=20220419)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_09131_gb300 import api
+    assert torch.cuda.is_available()
+    c = api.Context(0)
+    yield c.h
+    c.close()
+
+
+def _api():
+    from paper_2204_09131_gb300 import api
+    return api
+
+
+def _same(got, ref, what):
+    g = [(int(a), int(b)) for a, b in zip(got["t_s"], got["t_e"])]
+    r = [(a, b) for a, b, _, _ in ref]
+    assert g == r, (what, g[:10], r[:10])
+    for (a, b, sc, mi), gs, gm in zip(ref, got["score"], got["mi"]):
+        assert abs(gs - sc) <= TOL and abs(gm - mi) <= TOL, (what, a, b, gs, sc)
+
+
+@pytest.fixture(scope="module")
+def bench_oracle():
+    specs = [("planted", 2, p, PREFIX) for p in (0, 1)]
+    jobs = [(mode, sp, 0, PREFIX, BENCH_PARAMS) for sp in specs for mode in (0, 1)]
+    return specs, jobs, J.pool_map(J.search_job, jobs)
+
+
+def test_search_at_benchmark_settings_matches_oracle(ctx, bench_oracle):
+    """TD and BU queries of two 40k-point prefixes in one call, as the benchmark step runs
+    them; then with the sorted path forced for every window above 256 points, with brute
+    force only, and with incremental chains forced and off."""
+    api = _api()
+    specs, jobs, ref = bench_oracle
+    ids = []
+    for sp in specs:
+        x, y = J.series(sp)
+        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    api.isycos_autotune(ctx, 4)
+    queries = [(ids[specs.index(sp)][0], ids[specs.index(sp)][1], t0, t1, dict(prm, mode=mode))
+               for mode, sp, t0, t1, prm in jobs]
+    n_ref = sum(n for _, n in ref)
+    settings = [(0, 1), (0, 2), (2, 1), (1, 0)]   # (ISYCOS_OPT_KERNEL, ISYCOS_OPT_INCREMENTAL)
+    try:
+        for kern, incr in settings:
+            api.isycos_set_option(ctx, api.OPT_KERNEL, kern)
+            api.isycos_set_option(ctx, api.OPT_INCREMENTAL, incr)
+            api.isycos_reset_stats(ctx)
+            got = api.isycos_search_queries(ctx, queries)
+            st = api.isycos_get_stats(ctx)
+            for (mode, sp, _, _, _), g, (r, _) in zip(jobs, got, ref):
+                _same(g, r, (kern, incr, mode, sp))
+            assert st["decided_windows"] == n_ref, (kern, incr, st["decided_windows"], n_ref)
+            if incr == 1:
+                # the batched launches reached every window size of the layers (32 .. 4096)
+                assert all(st["windows_by_size"][b] > 0 for b in range(5, 13)), st["windows_by_size"]
+            if incr == 2:
+                assert st["incr_windows"] > 0
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+        api.isycos_set_option(ctx, api.OPT_INCREMENTAL, 1)
+    for a, b in ids:
+        api.isycos_drop_series(ctx, a)
+        api.isycos_drop_series(ctx, b)
+
+
+TIED_N = 200000
+
+
+@pytest.fixture(scope="module")
+def tied_oracle():
+    out = {}
+    for k in (3, 6):
+        wins = J.stratified_windows(k, TIED_N, 110, 12, seed=50 + k)
+        small = [(i, s, m) for i, (s, m) in enumerate(wins) if m <= 4096]
+        big = [(i, s, m) for i, (s, m) in enumerate(wins) if m > 4096]
+        # chunks of similar cost for the pool, pairs alternating by window index
+        jobs, where = [], []
+        for pair in (0, 1):
+            mine = [w for w in small if w[0] % 2 == pair]
+            mine.sort(key=lambda w: w[2])
+            for c in range(0, len(mine), 12):
+                chunk = mine[c:c + 12]
+                jobs.append((("tied", pair, TIED_N), k, [(s, m) for _, s, m in chunk]))
+                where.append([i for i, _, _ in chunk])
+        rng = np.random.default_rng(60 + k)
+        pjobs, pwhere = [], []
+        for i, s, m in big:
+            pts = np.unique(np.concatenate([[0, m - 1], rng.integers(0, m, 40)]))
+            pjobs.append((("tied", i % 2, TIED_N), k, s, m, [int(v) for v in pts]))
+            pwhere.append((i, pts))
+        res = J.pool_map(J.windows_job, jobs)
+        pres = J.pool_map(J.points_job, pjobs)
+        sums = {}
+        for idx, r in zip(where, res):
+            for i, v in zip(idx, r):
+                sums[i] = v
+        pts = {i: (p, r) for (i, p), r in zip(pwhere, pres)}
+        out[k] = (wins, sums, pts)
+    return out
+
+
+@pytest.mark.parametrize("k", [3, 6])
+def test_tied_windows_stratified_bit_exact(ctx, tied_oracle, k):
+    api = _api()
+    wins, sums, pts = tied_oracle[k]
+    assert len(wins) >= 1000 and len(sums) + len(pts) == len(wins)
+    ids = []
+    for pair in (0, 1):
+        x, y = J.series(("tied", pair, TIED_N))
+        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    xs = [ids[i % 2][0] for i in range(len(wins))]
+    ys = [ids[i % 2][1] for i in range(len(wins))]
+    w = api.windows_array(xs, ys, [s for s, _ in wins], [m for _, m in wins])
+    api.isycos_autotune(ctx, k)
+    out, nx, ny, c = api.isycos_mi_windows_points(ctx, w, k)
+    off = np.concatenate([[0], np.cumsum(w["m"].astype(np.int64))[:-1]])
+    for i, (s, m) in enumerate(wins):
+        if m <= 4096:
+            sp, sl, mi, hw, nmi = sums[i]
+            assert out["s_psi"][i] == sp and out["s_log"][i] == sl, (k, i, s, m)
+            assert abs(out["mi"][i] - mi) <= TOL and abs(out["h_w"][i] - hw) <= TOL
+            assert abs(out["nmi"][i] - nmi) <= TOL
+        else:
+            p, r = pts[i]
+            for j, (a, b, cc) in zip(p, r):
+                assert (nx[off[i] + j], ny[off[i] + j], c[off[i] + j]) == (a, b, cc), (k, i, m, j)
+    # every MI path gives the same integers (brute force only; sorted for 257..16384 points)
+    try:
+        for opt in (1, 2):
+            api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+            o2 = api.isycos_mi_windows(ctx, w, k)
+            bad = np.nonzero((o2["s_psi"] != out["s_psi"]) | (o2["s_log"] != out["s_log"]))[0]
+            assert bad.size == 0, (opt, bad[:8], w["m"][bad[:8]])
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+    for a, b in ids:
+        api.isycos_drop_series(ctx, a)
+        api.isycos_drop_series(ctx, b)
+
+
+MIXED_N = 30000
+MIXED_PARAMS = dict(k=4, s_min=32, s_max=8192, sigma=0.2, tau=0.05, seed=3)
+
+
+@pytest.fixture(scope="module")
+def mixed_oracle():
+    specs = [("mixed", 3, p, MIXED_N) for p in (0, 1)]
+    jobs = [(mode, sp, 0, MIXED_N, dict(MIXED_PARAMS, pruning=pr))
+            for sp in specs for mode in (0, 1) for pr in (0, 1)]
+    return specs, jobs, J.pool_map(J.search_job, jobs)
+
+
+def test_mixed_noise_pruning_on_and_off_match_oracle(ctx, mixed_oracle):
+    """Noise-pruning stress shape: each mode (pruning on, pruning off) equals the oracle in
+    that mode; the two modes may differ from each other (pruning is a heuristic)."""
+    api = _api()
+    specs, jobs, ref = mixed_oracle
+    ids = {}
+    for sp in specs:
+        x, y = J.series(sp)
+        ids[sp] = (api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y))
+    api.isycos_autotune(ctx, 4)
+    queries = [(ids[sp][0], ids[sp][1], t0, t1, dict(prm, mode=mode)) for mode, sp, t0, t1, prm in jobs]
+    api.isycos_reset_stats(ctx)
+    got = api.isycos_search_queries(ctx, queries)
+    st = api.isycos_get_stats(ctx)
+    for job, g, (r, _) in zip(jobs, got, ref):
+        _same(g, r, job[:2] + (job[4]["pruning"],))
+    assert st["decided_windows"] == sum(n for _, n in ref)
+    for a, b in ids.values():
+        api.isycos_drop_series(ctx, a)
+        api.isycos_drop_series(ctx, b)
+
+
+SERVE_N = 20000
+
+
+@pytest.fixture(scope="module")
+def serve_oracle():
+    rng = np.random.default_rng(17)
+    jobs = []
+    for i in range(10):
+        sp = ("planted", 4, i % 3, SERVE_N)
+        lo = int(rng.integers(0, 6000))
+        hi = int(rng.integers(lo + 2000, SERVE_N + 1))
+        prm = dict(k=4, s_min=32, s_max=1024, sigma=0.2, pruning=i % 2, seed=100 + i)
+        jobs.append((i % 2 if i < 8 else (i + 1) % 2, sp, lo, hi, prm))
+    return jobs, J.pool_map(J.search_job, jobs)
+
+
+def test_served_results_match_oracle(ctx, serve_oracle):
+    """Queries submitted all at once to the serving loop (continuous batching: they share
+    GPU batches as they run); each served result equals the oracle's search."""
+    api = _api()
+    jobs, ref = serve_oracle
+    ids = {}
+    for _, sp, _, _, _ in jobs:
+        if sp not in ids:
+            x, y = J.series(sp)
+            ids[sp] = (api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y))
+    tickets = [api.isycos_serve_submit(ctx, ids[sp][0], ids[sp][1], lo, hi, dict(prm, mode=mode))
+               for mode, sp, lo, hi, prm in jobs]
+    res = {}
+    deadline = time.time() + 300
+    while len(res) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in res:
+                r = api.isycos_serve_poll(ctx, t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    for job, t, (r, _) in zip(jobs, tickets, ref):
+        _same(res[t][0], r, job[:4])
+        assert res[t][1] > 0
+    for a, b in ids.values():
+        api.isycos_drop_series(ctx, a)
+        api.isycos_drop_series(ctx, b)
