@@ -384,7 +384,11 @@ def search_case(args):
             "kernel_ms": round(st["mi_kernel_ms"] / k, 2),
             "windows_by_size": [v // k for v in st["windows_by_size"]],
             "launches_by_size": [v // k for v in st["launches_by_size"]],
-            "launch_ms_by_size": [round(v / k, 2) for v in st["launch_ms_by_size"]]}
+            "launch_ms_by_size": [round(v / k, 2) for v in st["launch_ms_by_size"]],
+            "decided_by_size": [v // k for v in st["decided_by_size"]],
+            "dev_queries": st["dev_queries"] // k, "dev_rounds": st["dev_rounds"] // k,
+            "dev_cycles": [v // k for v in st["dev_cycles"]],
+            "work": {f: st[f] // k for f in ("work_bf", "work_scan", "work_search", "work_sort")}}
     print(json.dumps(line), flush=True)
     api.isycos_destroy(ctx)
 

@@ -147,7 +147,23 @@ typedef struct {
     int64_t windows_by_size[15];   /* batched windows evaluated                          */
     int64_t launches_by_size[15];  /* batched launches whose largest window is in b       */
     double launch_ms_by_size[15];  /* their event-timed durations, summed (not a union)   */
-} isycos_stats;   /* 440 bytes */
+    int64_t decided_by_size[15];   /* decided_windows by the same size buckets            */
+    /* Device-resident searches (ISYCOS_OPT_BU_DEVICE): */
+    int64_t dev_queries;           /* queries searched                                   */
+    int64_t dev_rounds;            /* decide / evaluate rounds, summed over queries      */
+    int64_t dev_cycles[3];         /* SM cycles of their CTAs in decide + ask, evaluate,
+                                      finish (clock64 of the CTA's first thread)          */
+    /* Work the MI kernels did, in the units of the method's own algorithm (the roofline of
+     * the work actually run, not of a brute-force equivalent): */
+    int64_t work_bf;               /* brute-force passes: point x candidate distance
+                                      evaluations (pass 1 and pass 2 count once together) */
+    int64_t work_scan;             /* sorted path, phase A: point x candidate visits of the
+                                      outward scans                                       */
+    int64_t work_search;           /* sorted path, phase B: binary-search steps and
+                                      duplicate-scan steps, per point                     */
+    int64_t work_sort;             /* sorted path: compare-exchange steps of the bitonic
+                                      sorts, per element pair                             */
+} isycos_stats;   /* 632 bytes */
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes caps the device memory the
  * context may hold for series and work buffers (0: 90% of the free memory at creation).
@@ -343,6 +359,21 @@ isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuning *out);
 #define ISYCOS_OPT_SPECULATION 7   /* SYCOS_BU: climbs whose first windows are asked ahead,
                                       assuming each ends where it starts; 0 .. 64 (default
                                       24).  Changes the GPU work only, never the results     */
+#define ISYCOS_OPT_BU_DEVICE 8     /* SYCOS_BU queries of isycos_search / _many / _queries:
+                                      1 the whole search runs on the GPU, one launch for all
+                                      BU queries of a call, every LAHC decision made on the
+                                      device next to the window MIs it reads (one CTA per
+                                      query); 0 (default) the host search machines, one launch
+                                      per round of all queries' windows over the whole GPU.
+                                      Same results either way; queries with h > 64,
+                                      t_max_idle > 31, chunks or selection, and every query
+                                      while ISYCOS_OPT_INCREMENTAL is 2, take the host
+                                      machines                                              */
+#define ISYCOS_OPT_TIME_LIMIT_MS 9 /* device-resident searches: a launch stops once it has run
+                                      this long (milliseconds, checked between rounds against
+                                      the GPU's global timer) and the call returns
+                                      ISYCOS_E_TIMEOUT with no windows; 0 = no limit (default
+                                      60000)                                                */
 isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value);
 
 /* Window MI that allocates nothing.  The paper has no counterpart: this entry point

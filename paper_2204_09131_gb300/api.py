@@ -34,6 +34,8 @@ OPT_SERVE_QUEUE = 4
 OPT_LANES = 5
 OPT_ESTIMATOR = 6
 OPT_SPECULATION = 7
+OPT_BU_DEVICE = 8
+OPT_TIME_LIMIT_MS = 9
 
 
 class IsycosError(RuntimeError):
@@ -87,7 +89,11 @@ class isycos_stats(ctypes.Structure):
                 ("queries_done", ctypes.c_int64), ("decided_windows", ctypes.c_int64),
                 ("mi_kernel_ms", ctypes.c_double), ("mi_kernel_launches", ctypes.c_int64),
                 ("windows_by_size", ctypes.c_int64 * 15), ("launches_by_size", ctypes.c_int64 * 15),
-                ("launch_ms_by_size", ctypes.c_double * 15)]
+                ("launch_ms_by_size", ctypes.c_double * 15),
+                ("decided_by_size", ctypes.c_int64 * 15), ("dev_queries", ctypes.c_int64),
+                ("dev_rounds", ctypes.c_int64), ("dev_cycles", ctypes.c_int64 * 3),
+                ("work_bf", ctypes.c_int64), ("work_scan", ctypes.c_int64),
+                ("work_search", ctypes.c_int64), ("work_sort", ctypes.c_int64)]
 
 
 # NumPy views of the C structs (same layout).

@@ -541,9 +541,12 @@ isycos_status isycos_destroy(isycos_ctx *ctx) {
     }
     DevBuf *bufs[] = {&ctx->d_series_ptr, &ctx->d_series_len, &ctx->d_table, &ctx->d_slot,
                       &ctx->d_pos, &ctx->d_bcount, &ctx->d_status, &ctx->d_plain_acc,
-                      &ctx->d_dev_items, &ctx->d_dev_queue, &ctx->d_dev_table};
+                      &ctx->d_dev_items, &ctx->d_dev_queue, &ctx->d_dev_table,
+                      &ctx->d_bu_q, &ctx->d_bu_res, &ctx->d_bu_found, &ctx->d_bu_queue};
     for (DevBuf *b : bufs) dev_release(ctx, *b);
     if (ctx->ev_ref) cudaEventDestroy(ctx->ev_ref);
+    if (ctx->ev_bu[0]) cudaEventDestroy(ctx->ev_bu[0]);
+    if (ctx->ev_bu[1]) cudaEventDestroy(ctx->ev_bu[1]);
     if (ctx->d_psi_fx) cudaFree(ctx->d_psi_fx);
     if (ctx->d_log_fx) cudaFree(ctx->d_log_fx);
     cudaStreamDestroy(ctx->stream);
@@ -913,6 +916,14 @@ isycos_status isycos_set_option(isycos_ctx *ctx, int32_t option, int64_t value) 
         case ISYCOS_OPT_SPECULATION:
             if (value < 0 || value > 64) break;
             ctx->opt_spec_climbs = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_BU_DEVICE:
+            if (value < 0 || value > 1) break;
+            ctx->opt_bu_device = (int)value;
+            return ISYCOS_OK;
+        case ISYCOS_OPT_TIME_LIMIT_MS:
+            if (value < 0 || value > 86400000) break;
+            ctx->opt_time_limit_ms = value;
             return ISYCOS_OK;
         default:
             return fail(ctx, ISYCOS_E_INVAL, "unknown option %d", option);

@@ -118,6 +118,10 @@ struct isycos_ctx {
     int opt_incremental = 1;
     int opt_estimator = 0;   // estimator of the direct window-MI entry points
     int opt_spec_climbs = 24; // SYCOS_BU climbs speculated ahead
+    int opt_bu_device = 0;    // SYCOS_BU on the device (bu_device.cu)
+    int64_t opt_time_limit_ms = 60000;   // device-resident searches: time limit per launch
+    isy::DevBuf d_bu_q, d_bu_res, d_bu_found, d_bu_queue;   // device SYCOS_BU
+    cudaEvent_t ev_bu[2] = {nullptr, nullptr};
     // sorted-path buckets chosen by isycos_autotune, per k (0: not tuned, use the default)
     uint32_t tuned_sort_mask[ISYCOS_MAX_K + 1] = {0};
     bool tuned[ISYCOS_MAX_K + 1] = {false};

@@ -19,6 +19,7 @@
 #include <unordered_map>
 
 #include "search.h"
+#include "bu_device.h"
 
 namespace isy {
 
@@ -755,6 +756,7 @@ private:
         // numbers far below 2^53, so their sums do not depend on the order).
         bool have = false;
         int64_t bs = 0, be = 0, n_read = 0;
+        int64_t by_size[kBuckets] = {};
         double pairs_read = 0.0;
         Val bv{0.0, 0.0};
         bool pure[2] = {false, false};   // candidates (-r, 0) and (0, r): the pure extensions
@@ -768,6 +770,7 @@ private:
                 if (!grid_.get(ac + a, bc + b, &v)) return false;
                 const int64_t m = te - ts + 1;
                 ++n_read;
+                ++by_size[size_bucket((int)m)];
                 pairs_read += (double)m * (double)(m - 1);
                 if (!have || v.score > bv.score) {        // first maximum wins
                     have = true;
@@ -795,6 +798,7 @@ private:
         }
         // every score is at hand: the step
         evals += n_read;
+        for (int b = 0; b < kBuckets; ++b) evals_by_size[b] += by_size[b];
         cost += pairs_read;
         if (prm.pruning) {
             for (int sd = 0; sd < 2; ++sd) {
@@ -906,7 +910,9 @@ public:
         std::vector<WinReq> r;
         if (!final_->want(r)) {
             found = final_->found;
-            evals = final_->evals + sub_evals_;
+            clear_evals();
+            add_evals(*final_);
+            add_evals(sub_evals_);
             cost = final_->cost;
             return false;
         }
@@ -960,11 +966,11 @@ public:
 private:
     void select() {
         double t_td = 0.0, t_bu = 0.0, nl_td = 0.0, ns_bu = 0.0;
-        sub_evals_ = 0;
+        sub_evals_.clear_evals();
         for (size_t i = 0; i < subs_.size(); ++i) {
             const SearchMachine &m = *subs_[i];
             const bool td = (i % 2) == 0;
-            sub_evals_ += m.evals;
+            sub_evals_.add_evals(m);
             (td ? t_td : t_bu) += m.cost;
             for (const auto &w : m.found) {
                 const bool small = (double)(w.t_e - w.t_s + 1) <= prm.sel_rho * (double)prm.s_max;
@@ -992,7 +998,11 @@ private:
 
     int phase_ = 0;
     int n_samples_ = 0;
-    int64_t sub_evals_ = 0;
+    // evaluation counts of the sampled searches (a machine that never runs, used as a tally)
+    struct Tally : SearchMachine {
+        bool want(std::vector<WinReq> &) override { return false; }
+        void give(const isycos_mi_out *, size_t) override {}
+    } sub_evals_;
     std::vector<std::unique_ptr<SearchMachine>> subs_;
     std::vector<bool> sub_done_;
     std::vector<std::pair<size_t, size_t>> from_;
@@ -1033,11 +1043,11 @@ public:
         }
         if (any) return true;
         found.clear();
-        evals = 0;
+        clear_evals();
         cost = 0.0;
         for (const auto &m : subs_) {
             found.insert(found.end(), m->found.begin(), m->found.end());
-            evals += m->evals;
+            add_evals(*m);
             cost += m->cost;
         }
         std::stable_sort(found.begin(), found.end(),
@@ -1318,6 +1328,169 @@ isycos_status isycos_search(isycos_ctx *ctx, int32_t xs, int32_t ys, int64_t t_b
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------------------
+// SYCOS_BU on the device (bu_device.cu): all eligible BU queries of a call in one launch per
+// k, started before the host lanes run the other queries and collected after them.
+// ---------------------------------------------------------------------------------------
+struct BuDeviceRun {
+    std::vector<int64_t> idx;            // query indices of the call, grouped by k
+    std::vector<int> group_k;
+    std::vector<int64_t> group_off;
+    int64_t cap = 0;
+    bool open = false;
+    cudaStream_t st = nullptr;
+    std::vector<DevBuResult> res;
+};
+
+static bool bu_device_eligible(const isycos_ctx *ctx, const SearchParams &p) {
+    // (ISYCOS_OPT_INCREMENTAL = 2 asks for the incremental chains, which only the host
+    // machines form)
+    return ctx->opt_bu_device && ctx->opt_incremental != 2 && p.mode == 1 && p.chunks <= 1 &&
+           p.h <= kBuMaxH && p.t_max_idle <= kBuMaxIdle;
+}
+
+static isycos_status bu_device_begin(isycos_ctx *ctx, BuDeviceRun &R, const int32_t *xs,
+                                     const int32_t *ys, const int64_t *t_begin,
+                                     const int64_t *t_end, const SearchParams *prm,
+                                     size_t prm_stride, int64_t cap) {
+    std::stable_sort(R.idx.begin(), R.idx.end(), [&](int64_t a, int64_t b) {
+        return prm[a * prm_stride].k < prm[b * prm_stride].k;
+    });
+    const size_t n = R.idx.size();
+    std::vector<DevBuQuery> qs(n);
+    for (size_t i = 0; i < n; ++i) {
+        const int64_t q = R.idx[i];
+        const SearchParams &p = prm[q * prm_stride];
+        DevBuQuery &d = qs[i];
+        d.x = ctx->series_ptr[xs[q]];
+        d.y = ctx->series_ptr[ys[q]];
+        d.t_begin = t_begin[q];
+        d.t_end = t_end[q];
+        d.sigma = p.sigma;
+        d.tau = p.tau;
+        d.seed = p.seed;
+        d.k = p.k;
+        d.score_kind = p.score_kind;
+        d.s_min = p.s_min;
+        d.s_max = p.s_max;
+        d.delta = p.delta_bu;
+        d.h = p.h;
+        d.t_max_idle = p.t_max_idle;
+        d.p = p.p;
+        d.pruning = p.pruning;
+        d.max_steps = p.max_steps;
+        d.est = p.estimator;
+        d.pad = 0;
+        if (i == 0 || qs[i - 1].k != d.k) {
+            R.group_k.push_back(d.k);
+            R.group_off.push_back((int64_t)i);
+        }
+    }
+    R.group_off.push_back((int64_t)n);
+    R.cap = std::max<int64_t>(1, cap);
+    isycos_status rc;
+    Lane *L = nullptr;
+    if ((rc = get_lane(ctx, kLaneSlots - 1, &L))) return rc;   // highest stream priority
+    R.st = L->stream;
+    std::vector<int> grids;
+    for (size_t g = 0; g < R.group_k.size(); ++g) {
+        int per_sm = 0;
+        cudaError_t e = bu_device_prepare(R.group_k[g], &per_sm);
+        if (e != cudaSuccess || per_sm < 1) return cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "device SYCOS_BU setup");
+        const int64_t nq = R.group_off[g + 1] - R.group_off[g];
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)ctx->n_sm * per_sm));
+        grids.push_back(grid);
+    }
+    const size_t n_groups = R.group_k.size();
+    if ((rc = dev_reserve(ctx, ctx->d_bu_q, sizeof(DevBuQuery) * n))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_bu_res, sizeof(DevBuResult) * n))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_bu_found, sizeof(isycos_result_window) * n * (size_t)R.cap))) return rc;
+    if ((rc = dev_reserve(ctx, ctx->d_bu_queue, 4 * n_groups + 16))) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->ev_bu[0]) e = cudaEventCreate(&ctx->ev_bu[0]);
+    if (e == cudaSuccess && !ctx->ev_bu[1]) e = cudaEventCreate(&ctx->ev_bu[1]);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_bu_q.p, qs.data(), sizeof(DevBuQuery) * n, cudaMemcpyHostToDevice, R.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_bu_queue.p, 0, 4 * n_groups, R.st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_bu[0], R.st);
+    for (size_t g = 0; g < n_groups && e == cudaSuccess; ++g) {
+        BuLaunch a;
+        const int64_t off = R.group_off[g];
+        a.q = reinterpret_cast<const DevBuQuery *>(ctx->d_bu_q.p) + off;
+        a.n_q = (int32_t)(R.group_off[g + 1] - off);
+        a.spec_climbs = ctx->opt_spec_climbs;
+        a.res = reinterpret_cast<DevBuResult *>(ctx->d_bu_res.p) + off;
+        a.found = reinterpret_cast<isycos_result_window *>(ctx->d_bu_found.p) + off * R.cap;
+        a.cap = R.cap;
+        a.queue = reinterpret_cast<int32_t *>(ctx->d_bu_queue.p) + g;
+        a.psi_fx = ctx->d_psi_fx;
+        a.log_fx = ctx->d_log_fx;
+        a.limit_ns = (uint64_t)ctx->opt_time_limit_ms * 1000000ull;
+        e = bu_device_launch(a, R.group_k[g], grids[g], R.st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_bu[1], R.st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device SYCOS_BU launch");
+    R.open = true;
+    return ISYCOS_OK;
+}
+
+// Wait for the device searches and fetch their windows into found[i] (query R.idx[i]).
+static isycos_status bu_device_end(isycos_ctx *ctx, BuDeviceRun &R,
+                                   std::vector<std::vector<isycos_result_window>> &found,
+                                   int64_t *decided) {
+    if (!R.open) return ISYCOS_OK;
+    R.open = false;
+    const size_t n = R.idx.size();
+    R.res.resize(n);
+    cudaError_t e = cudaMemcpyAsync(R.res.data(), ctx->d_bu_res.p, sizeof(DevBuResult) * n,
+                                    cudaMemcpyDeviceToHost, R.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(R.st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device SYCOS_BU");
+    found.assign(n, {});
+    bool timeout = false;
+    int64_t windows = 0, pairs = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const DevBuResult &r = R.res[i];
+        timeout |= r.status != 0;
+        const int64_t keep = std::min<int64_t>(r.n_found, R.cap);
+        found[i].resize((size_t)r.n_found);
+        if (keep > 0)
+            e = cudaMemcpyAsync(found[i].data(),
+                                reinterpret_cast<isycos_result_window *>(ctx->d_bu_found.p) + (int64_t)i * R.cap,
+                                sizeof(isycos_result_window) * (size_t)keep, cudaMemcpyDeviceToHost, R.st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "device SYCOS_BU results");
+        windows += r.windows;
+        pairs += r.pairs;
+        *decided += r.evals;
+    }
+    e = cudaStreamSynchronize(R.st);
+    float t0 = 0.0f, t1 = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ctx->ev_ref, ctx->ev_bu[0]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev_ref, ctx->ev_bu[1]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device SYCOS_BU results");
+    add_stats(ctx, windows, pairs, (int64_t)R.group_k.size(), 1, 0);
+    {
+        std::lock_guard<std::mutex> g(ctx->stats_mu);
+        ctx->kernel_iv.push_back({t0, t1});
+        ctx->stats.mi_kernel_launches += (int64_t)R.group_k.size();
+        ctx->stats.dev_queries += (int64_t)n;
+        for (size_t i = 0; i < n; ++i) {
+            const DevBuResult &r = R.res[i];
+            for (int b = 0; b < kBuckets; ++b) {
+                ctx->stats.windows_by_size[b] += r.windows_by_size[b];
+                ctx->stats.decided_by_size[b] += r.evals_by_size[b];
+            }
+            ctx->stats.dev_rounds += r.rounds;
+            for (int j = 0; j < 3; ++j) ctx->stats.dev_cycles[j] += r.cycles[j];
+            ctx->stats.work_bf += r.work_bf;
+        }
+    }
+    if (timeout)
+        return fail(ctx, ISYCOS_E_TIMEOUT, "device SYCOS_BU: the time limit of %lld ms ran out",
+                    (long long)ctx->opt_time_limit_ms);
+    return ISYCOS_OK;
+}
+
 // Run independent queries (each with its own parameters) to completion.
 static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs, const int32_t *ys,
                                  const int64_t *t_begin, const int64_t *t_end,
@@ -1326,15 +1499,28 @@ static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     isycos_status rc;
     std::vector<std::unique_ptr<SearchMachine>> own;
     std::vector<SearchMachine *> ms;
+    std::vector<int64_t> host_of((size_t)n_q, -1);   // index into ms, or -1: on the device
+    BuDeviceRun bu;
     for (int64_t q = 0; q < n_q; ++q) {
         if ((rc = check_query(ctx, xs[q], ys[q], t_begin[q], t_end[q]))) return rc;
+        if (bu_device_eligible(ctx, prm[q * prm_stride])) {
+            bu.idx.push_back(q);
+            continue;
+        }
         own.push_back(make_machine(xs[q], ys[q], t_begin[q], t_end[q], prm[q * prm_stride]));
+        host_of[q] = (int64_t)ms.size();
         ms.push_back(own.back().get());
+    }
+    // the device searches start first, on the highest-priority stream, so that their CTAs
+    // take their SMs before the host lanes' launches fill the GPU
+    if (!bu.idx.empty()) {
+        if ((rc = bu_device_begin(ctx, bu, xs, ys, t_begin, t_end, prm, prm_stride, cap_per_query)))
+            return rc;
     }
     // Independent queries split over engine lanes, one host thread per lane: each thread runs
     // its machines' rounds on its own stream, so that the sequential decision logic of many
     // queries proceeds in parallel and their batches overlap on the GPU.
-    const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, (n_q + 3) / 4));
+    const int n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, ((int64_t)ms.size() + 3) / 4));
     // SYCOS_TD queries make few, large launches (throughput-bound); the others many small
     // ones (latency-bound).  When both are present they get separate lanes: the TD lanes'
     // launches leave a quarter of the GPU's CTA slots free and the others run on
@@ -1371,19 +1557,27 @@ static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
             cudaSetDevice(dev);
             st[i] = run_machines(ctx, *lanes[i], parts[i], lanes[i]->stream);
         });
-    st[0] = run_machines(ctx, *lanes[0], parts[0], lanes[0]->stream);
+    if (!ms.empty()) st[0] = run_machines(ctx, *lanes[0], parts[0], lanes[0]->stream);
     for (auto &t : th) t.join();
+    std::vector<std::vector<isycos_result_window>> dev_found;
+    int64_t decided = 0;
+    const isycos_status st_bu = bu_device_end(ctx, bu, dev_found, &decided);
     for (isycos_status s1 : st)
         if (s1) return s1;
+    if (st_bu) return st_bu;
+    std::vector<int64_t> dev_of((size_t)n_q, -1);
+    for (size_t i = 0; i < bu.idx.size(); ++i) dev_of[bu.idx[i]] = (int64_t)i;
     isycos_status result = ISYCOS_OK;
     {
-        int64_t decided = 0;
-        for (SearchMachine *m : ms) decided += m->evals;
         std::lock_guard<std::mutex> g2(ctx->stats_mu);
+        for (SearchMachine *m : ms) {
+            decided += m->evals;
+            for (int b = 0; b < kBuckets; ++b) ctx->stats.decided_by_size[b] += m->evals_by_size[b];
+        }
         ctx->stats.decided_windows += decided;
     }
     for (int64_t q = 0; q < n_q; ++q) {
-        const auto &f = ms[q]->found;
+        const auto &f = host_of[q] >= 0 ? ms[host_of[q]]->found : dev_found[dev_of[q]];
         n_out[q] = (int64_t)f.size();
         if ((int64_t)f.size() > cap_per_query) {
             result = fail(ctx, ISYCOS_E_TRUNC, "query %lld found %lld windows, capacity %lld",

@@ -53,11 +53,23 @@ public:
     SearchParams prm{};
     std::vector<isycos_result_window> found;
     int64_t evals = 0;       // window scores consumed by the decisions
+    int64_t evals_by_size[kBuckets] = {};   // the same by size bucket (m <= 2^b)
     double cost = 0.0;       // their pair comparisons, sum m (m - 1): the search's "runtime"
+
+    // Take over another machine's evaluation counts (sub-searches of selection and chunks).
+    void add_evals(const SearchMachine &o) {
+        evals += o.evals;
+        for (int b = 0; b < kBuckets; ++b) evals_by_size[b] += o.evals_by_size[b];
+    }
+    void clear_evals() {
+        evals = 0;
+        for (int b = 0; b < kBuckets; ++b) evals_by_size[b] = 0;
+    }
 
 protected:
     void count(int64_t m) {
         ++evals;
+        ++evals_by_size[size_bucket((int)m)];
         cost += (double)m * (double)(m - 1);
     }
     double score_of(const isycos_mi_out &r) const { return prm.score_kind == 1 ? r.mi : r.nmi; }

@@ -200,6 +200,7 @@ private:
             q->result = q->sm->found;
             std::lock_guard<std::mutex> g(ctx_->stats_mu);
             ctx_->stats.decided_windows += q->sm->evals;
+            for (int b = 0; b < kBuckets; ++b) ctx_->stats.decided_by_size[b] += q->sm->evals_by_size[b];
         }
         q->sm.reset();
         reserved_ -= q->bytes;

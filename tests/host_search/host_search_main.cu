@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "search.h"
+#include "bu_device.h"
 
 extern "C" {
 // The oracle's window estimator (see oracle/isycos_oracle.c for its contract).
@@ -76,6 +77,12 @@ isycos_status fail(isycos_ctx *, isycos_status st, const char *fmt, ...) {
     return st;
 }
 isycos_status cuda_fail(isycos_ctx *, cudaError_t, const char *) { return ISYCOS_E_CUDA; }
+// The device-resident search and the buffer / statistics helpers it calls are not used by
+// this harness (it drives the machines directly); they only have to link.
+isycos_status dev_reserve(isycos_ctx *, DevBuf &, size_t) { return ISYCOS_E_NOMEM; }
+cudaError_t bu_device_prepare(int, int *) { return cudaErrorNotSupported; }
+cudaError_t bu_device_launch(const BuLaunch &, int, int, cudaStream_t) { return cudaErrorNotSupported; }
+void add_stats(isycos_ctx *, int64_t, int64_t, int64_t, int64_t, int64_t) {}
 isycos_status get_lane(isycos_ctx *, int, Lane **) { return ISYCOS_E_INVAL; }
 isycos_status engine_launch(isycos_ctx *, Lane &L, const HostWindow *w, int64_t n, int k, int est,
                             int32_t *, int32_t *, int32_t *, cudaStream_t) {

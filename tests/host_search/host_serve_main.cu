@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "search.h"
+#include "bu_device.h"
 
 extern "C" {
 typedef struct {
@@ -56,6 +57,12 @@ isycos_status score(int32_t xs, int32_t ys, int64_t start, int32_t m, int k, int
 namespace isy {
 isycos_status fail(isycos_ctx *, isycos_status st, const char *, ...) { return st; }
 isycos_status cuda_fail(isycos_ctx *, cudaError_t, const char *) { return ISYCOS_E_CUDA; }
+// The device-resident search and the buffer / statistics helpers it calls are not used by
+// this harness (it drives the machines directly); they only have to link.
+isycos_status dev_reserve(isycos_ctx *, DevBuf &, size_t) { return ISYCOS_E_NOMEM; }
+cudaError_t bu_device_prepare(int, int *) { return cudaErrorNotSupported; }
+cudaError_t bu_device_launch(const BuLaunch &, int, int, cudaStream_t) { return cudaErrorNotSupported; }
+void add_stats(isycos_ctx *, int64_t, int64_t, int64_t, int64_t, int64_t) {}
 static Lane g_lanes[kLaneSlots];
 isycos_status get_lane(isycos_ctx *, int i, Lane **out) {
     if (i < 0 || i >= kLaneSlots) return ISYCOS_E_INVAL;
@@ -134,6 +141,7 @@ int main(int argc, char **argv) {
     auto ctx = std::make_unique<isycos_ctx>();
     ctx->budget = (uint64_t)1 << 40;
     ctx->max_lanes = 4;
+    ctx->opt_bu_device = 0;   // the host search machines (the device search needs a GPU)
     ctx->serve_slots = 6;   // fewer slots than queries: admission waits for retirements
     for (int32_t p = 0; p < n_pairs; ++p) {   // resident series: the host copies stand in
         ctx->series_ptr.push_back(g_x[(size_t)p].data());

@@ -46,7 +46,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(api.isycos_mi_out) == 40
     assert ctypes.sizeof(api.isycos_result_window) == 32
     assert ctypes.sizeof(api.isycos_params) == 104
-    assert ctypes.sizeof(api.isycos_stats) == 440
+    assert ctypes.sizeof(api.isycos_stats) == 632
     assert ctypes.sizeof(api.isycos_tuning) == 312
 
 

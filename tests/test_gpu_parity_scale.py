@@ -75,18 +75,21 @@ def test_search_at_benchmark_settings_matches_oracle(ctx, bench_oracle):
     queries = [(ids[specs.index(sp)][0], ids[specs.index(sp)][1], t0, t1, dict(prm, mode=mode))
                for mode, sp, t0, t1, prm in jobs]
     n_ref = sum(n for _, n in ref)
-    settings = [(0, 1), (0, 2), (2, 1), (1, 0)]   # (ISYCOS_OPT_KERNEL, ISYCOS_OPT_INCREMENTAL)
+    # (ISYCOS_OPT_KERNEL, ISYCOS_OPT_INCREMENTAL, ISYCOS_OPT_BU_DEVICE)
+    settings = [(0, 1, 0), (0, 2, 0), (2, 1, 0), (1, 0, 0), (0, 1, 1)]
     try:
-        for kern, incr in settings:
+        for kern, incr, dev in settings:
             api.isycos_set_option(ctx, api.OPT_KERNEL, kern)
             api.isycos_set_option(ctx, api.OPT_INCREMENTAL, incr)
+            api.isycos_set_option(ctx, api.OPT_BU_DEVICE, dev)
             api.isycos_reset_stats(ctx)
             got = api.isycos_search_queries(ctx, queries)
             st = api.isycos_get_stats(ctx)
             for (mode, sp, _, _, _), g, (r, _) in zip(jobs, got, ref):
                 _same(g, r, (kern, incr, mode, sp))
-            assert st["decided_windows"] == n_ref, (kern, incr, st["decided_windows"], n_ref)
-            if incr == 1:
+            assert st["decided_windows"] == n_ref, (kern, incr, dev, st["decided_windows"], n_ref)
+            assert sum(st["decided_by_size"]) == n_ref
+            if incr == 1 and not dev:
                 # the batched launches reached every window size of the layers (32 .. 4096)
                 assert all(st["windows_by_size"][b] > 0 for b in range(5, 13)), st["windows_by_size"]
             if incr == 2:
@@ -94,6 +97,7 @@ def test_search_at_benchmark_settings_matches_oracle(ctx, bench_oracle):
     finally:
         api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
         api.isycos_set_option(ctx, api.OPT_INCREMENTAL, 1)
+        api.isycos_set_option(ctx, api.OPT_BU_DEVICE, 0)
     for a, b in ids:
         api.isycos_drop_series(ctx, a)
         api.isycos_drop_series(ctx, b)

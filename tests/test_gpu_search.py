@@ -374,19 +374,23 @@ def test_speculation_depth_changes_work_not_results(ctx):
     okw = dict(kw)
     okw.pop("mode")
     ref, n = O.search_bu(x, y, **okw)
-    launches = {}
+    launches = {1: {}, 0: {}}
     try:
-        for depth in (0, 1, 3, 8, 16, 24, 64):
-            api.isycos_set_option(ctx, api.OPT_SPECULATION, depth)
-            api.isycos_reset_stats(ctx)
-            got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
-            st = api.isycos_get_stats(ctx)
-            _same(got, ref)
-            assert st["decided_windows"] == n
-            launches[depth] = st["launches"]
+        for dev in (1, 0):   # the device-resident search, then the host machines
+            api.isycos_set_option(ctx, api.OPT_BU_DEVICE, dev)
+            for depth in (0, 1, 3, 8, 16, 24, 64):
+                api.isycos_set_option(ctx, api.OPT_SPECULATION, depth)
+                api.isycos_reset_stats(ctx)
+                got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+                st = api.isycos_get_stats(ctx)
+                _same(got, ref)
+                assert st["decided_windows"] == n
+                launches[dev][depth] = st["launches"]
     finally:
         api.isycos_set_option(ctx, api.OPT_SPECULATION, 24)   # the default
-    assert launches[3] < launches[0]
+        api.isycos_set_option(ctx, api.OPT_BU_DEVICE, 0)
+    assert launches[0][3] < launches[0][0]                  # host: fewer round trips
+    assert all(v == 1 for v in launches[1].values())        # device: one launch
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
 
@@ -470,3 +474,56 @@ def test_series_added_while_queries_are_served(ctx):
         assert np.array_equal(api.isycos_search(ctx, *q, prm), res[t][0])
     for e in extra:
         api.isycos_drop_series(ctx, e)
+
+
+@pytest.mark.parametrize("extra", PARAMS[2:4] + PARAMS[5:6] + PARAMS[7:8],
+                         ids=lambda d: ",".join("%s=%s" % kv for kv in d.items()))
+def test_bu_on_the_device_and_on_the_host_match_oracle(ctx, extra):
+    """SYCOS_BU with every decision on the device (one launch per call) and with the host
+    search machines (one launch per round): both equal the oracle, with the same
+    decided-window counts."""
+    api = _api()
+    x, y = synth.planted_small_pair()
+    kw = dict(k=4, s_min=32, s_max=256, sigma=0.2, seed=11)
+    kw.update(extra)
+    ref, n = O.search_bu(x, y, **{k: v for k, v in kw.items() if k != "mode"})
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    try:
+        for dev in (1, 0):
+            api.isycos_set_option(ctx, api.OPT_BU_DEVICE, dev)
+            api.isycos_reset_stats(ctx)
+            got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+            st = api.isycos_get_stats(ctx)
+            _same(got, ref)
+            assert st["decided_windows"] == n, (dev, st["decided_windows"], n)
+            if dev:
+                assert st["launches"] == 1
+    finally:
+        api.isycos_set_option(ctx, api.OPT_BU_DEVICE, 0)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
+
+
+def test_device_search_time_limit_returns_timeout(ctx):
+    """A device-resident search that runs past its time limit stops between rounds and the
+    call returns ISYCOS_E_TIMEOUT; the context stays usable and the next call (no limit)
+    returns the oracle's windows."""
+    api = _api()
+    x, y, _ = synth.planted_pair(2, 3, 60000)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    kw = dict(k=4, s_min=32, s_max=1024, sigma=0.2, pruning=1, seed=5, mode=1)
+    api.isycos_set_option(ctx, api.OPT_BU_DEVICE, 1)
+    try:
+        api.isycos_set_option(ctx, api.OPT_TIME_LIMIT_MS, 1)
+        with pytest.raises(api.IsycosError) as e:
+            api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+        assert e.value.status == api.E_TIMEOUT
+        api.isycos_set_option(ctx, api.OPT_TIME_LIMIT_MS, 60000)
+        got = api.isycos_search(ctx, xs, ys, 0, len(x), kw)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_TIME_LIMIT_MS, 60000)
+        api.isycos_set_option(ctx, api.OPT_BU_DEVICE, 0)
+    ref, _ = O.search_bu(x, y, **{k: v for k, v in kw.items() if k != "mode"})
+    _same(got, ref)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
