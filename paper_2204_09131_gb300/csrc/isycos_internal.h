@@ -67,6 +67,10 @@ struct BatchArgs {
     double inv_k;                // 1 / k correctly rounded (estimator 0), or 0 (estimator 1)
     unsigned char *gscratch;     // sorted-path scratch of windows above kSortMax points: one
     int64_t gscratch_stride;     // slice of gscratch_stride bytes per CTA (nullptr: none)
+    // Work counters of the sorted path (nullptr: not counted): device accumulators, zero at
+    // launch, which the last CTA copies to work_out and zeroes again.
+    unsigned long long *work = nullptr;      // [0] phase A point x candidate visits, [1] phase B steps
+    unsigned long long *work_out = nullptr;
 };
 
 // Device-side preparation of a window list held in device memory.
@@ -171,6 +175,29 @@ __host__ __device__ inline size_t sorted_scratch(int m) {   // the part after th
     return (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16;
 }
 __host__ __device__ inline size_t sorted_smem(int m) { return sorted_off(m) + sorted_scratch(m); }
+
+// Work the brute-force and sort parts of a launch do, known from the window sizes alone
+// (the data-dependent parts are counted on the device):
+//  - a window on the brute-force path: m x m point x candidate distance evaluations per pass
+//    (the point itself included);
+//  - a window on the sorted path: the compare-exchange steps of its two bitonic sorts over
+//    N = 2^ceil(log2 m) slots, each (N / 2) x log2(N) x (log2(N) + 1) / 2 (both together are
+//    returned).
+__host__ __device__ inline long long sort_cx_steps(int m) {
+    int lg = 0;
+    while ((1 << lg) < m) ++lg;
+    const long long N = 1ll << lg;
+    return N * (long long)lg * (long long)(lg + 1) / 2;
+}
+// Whether a window of m points in a launch of nt-thread CTAs takes the sorted path (the
+// batched kernel's rule: windows of more than 64 points that run one per CTA, in a bucket of
+// sort_mask, with their scratch in shared memory or in the launch's global scratch).
+__host__ __device__ inline bool takes_sorted_path(int m, int nt, uint32_t sort_mask, bool gscratch) {
+    if (m <= 64) return false;
+    const int q = kBuckets - 1 - size_bucket(m);
+    const bool one_per_cta = nt / 32 / warps_per_item(q, nt) == 1;
+    return one_per_cta && ((sort_mask >> size_bucket(m)) & 1u) && (m <= kSortMax || gscratch);
+}
 
 // Shared memory of a batched launch whose largest window has max_m points; max_sorted is the
 // largest window that takes the sorted path (0: none).

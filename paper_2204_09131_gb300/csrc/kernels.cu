@@ -177,12 +177,14 @@ __host__ __device__ inline int pow2_ceil(int m) {
     return n;
 }
 
+// work (optional): [0] += phase A point x candidate visits, [1] += phase B search and
+// duplicate-scan steps.
 template <int K1, int NT>
 __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned char *scratch,
                                   const long long *__restrict__ psi_fx,
                                   const long long *__restrict__ log_fx, long long &acc_psi,
                                   long long &acc_log, int32_t *nx_out, int32_t *ny_out,
-                                  int32_t *c_out, int est) {
+                                  int32_t *c_out, int est, unsigned long long *work) {
     const float kInf = __int_as_float(0x7f800000);
     const int N = pow2_ceil(m);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
@@ -220,6 +222,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     {
         const int lane = threadIdx.x & 31;
         const int n_chunks = (m + 31) >> 5;
+        unsigned long long visits = 0;   // this warp's point x candidate visits
         for (;;) {
             int chunk = 0;
             if (lane == 0) chunk = atomicAdd(ctr, 1);
@@ -299,6 +302,8 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                     }
                 }
             }
+            // candidates visited: [L + 1, R), for the chunk's valid points
+            visits += (unsigned long long)(R - L - 1) * (unsigned long long)min(32, m - c0);
             if (valid) {
                 float dxm = 0.0f, dym = 0.0f;
                 int cc = 0;
@@ -318,9 +323,11 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
             }
         }
+        if (work && lane == 0) atomicAdd(work, visits);
     }
     __syncthreads();
     // Phase B: the marginal counts by binary search, and the duplicate counts left open.
+    int steps = 0;   // this thread's search and scan steps
     for (int t = threadIdx.x; t < m; t += NT) {
         const float4 me = rec[t];
         const float xi = me.x, yi = me.y;
@@ -329,12 +336,14 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
         // n_x: the x-sorted range around position t where fabsf(x_i - x) <= d_x
         int l0 = 0, l1 = t;
         while (l0 < l1) {
+            ++steps;
             const int mid = (l0 + l1) >> 1;
             if (fabsf(xi - rec[mid].x) <= dxm) l1 = mid;
             else l0 = mid + 1;
         }
         int r0 = t, r1 = m - 1;
         while (r0 < r1) {
+            ++steps;
             const int mid = (r0 + r1 + 1) >> 1;
             if (fabsf(xi - rec[mid].x) <= dxm) r0 = mid;
             else r1 = mid - 1;
@@ -343,6 +352,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
         // n_y: the same on the y-sorted values, around the first value >= y_i
         int p0 = 0, p1 = m;
         while (p0 < p1) {
+            ++steps;
             const int mid = (p0 + p1) >> 1;
             if (ys[mid] < yi) p0 = mid + 1;
             else p1 = mid;
@@ -350,12 +360,14 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
         const int piv = p0;
         int q0 = 0, q1 = piv;
         while (q0 < q1) {
+            ++steps;
             const int mid = (q0 + q1) >> 1;
             if (fabsf(yi - ys[mid]) <= dym) q1 = mid;
             else q0 = mid + 1;
         }
         int w0 = piv, w1 = m - 1;
         while (w0 < w1) {
+            ++steps;
             const int mid = (w0 + w1 + 1) >> 1;
             if (fabsf(yi - ys[mid]) <= dym) w0 = mid;
             else w1 = mid - 1;
@@ -364,8 +376,8 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
         int cc = pcc[t];
         if (cc < 0) {   // k+1-th distance 0: count the duplicates among the equal x values
             cc = 1;
-            for (int u = t - 1; u >= 0 && rec[u].x == xi; --u) cc += rec[u].y == yi ? 1 : 0;
-            for (int u = t + 1; u < m && rec[u].x == xi; ++u) cc += rec[u].y == yi ? 1 : 0;
+            for (int u = t - 1; u >= 0 && rec[u].x == xi; --u, ++steps) cc += rec[u].y == yi ? 1 : 0;
+            for (int u = t + 1; u < m && rec[u].x == xi; ++u, ++steps) cc += rec[u].y == yi ? 1 : 0;
         }
         // (an empty strip, t < 0, leaves the search ranges at the point itself: count 1)
         const int nxv = cx - 1, nyv = cy - 1;
@@ -376,6 +388,12 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
             ny_out[ji] = nyv;
             c_out[ji] = cc;
         }
+    }
+    if (work) {
+        unsigned long long w = (unsigned long long)steps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(work + 1, w);
     }
 }
 
@@ -430,7 +448,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                 unsigned char *scr = it.m <= kSortMax
                                          ? reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m)
                                          : a.gscratch + (size_t)blockIdx.x * (size_t)a.gscratch_stride;
-                ksg_window_sorted<K1, NT>(s, it.m, scr, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est);
+                ksg_window_sorted<K1, NT>(s, it.m, scr, a.psi_fx, a.log_fx, lp, ll, nxo, nyo, co, a.est,
+                                          a.work);
             } else {
                 const int nblk = (it.m + kBlockPts - 1) / kBlockPts;
                 for (int b = sub; b < nblk; b += wpw)
@@ -492,6 +511,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         write_result(a.out + pend_out, a.k, pend_m, pend_psi, pend_log, a.psi_fx, a.log_fx, a.inv_k);
     // The last CTA to finish zeroes the work counters for the next launch on this buffer:
     // every other CTA has taken its last job before it counts itself out.
+    // (the work counters this CTA added are ordered before its count by the fence)
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -499,7 +520,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
             a.queue[0] = 0;
             a.queue[1] = 0;
             a.queue[2] = 0;
-            __threadfence();
+            if (a.work) {
+                a.work_out[0] = atomicExch(a.work, 0ull);
+                a.work_out[1] = atomicExch(a.work + 1, 0ull);
+            }
+            __threadfence_system();
         }
     }
 }

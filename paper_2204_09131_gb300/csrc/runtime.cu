@@ -205,7 +205,9 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     const size_t tab_bytes = (sizeof(BucketTable) + 255) & ~(size_t)255;
     const size_t stage_bytes = tab_bytes + sizeof(WorkItem) * n;
     if ((rc = host_reserve(ctx, L.h_items, stage_bytes))) return rc;
-    if ((rc = host_reserve(ctx, L.h_table, sizeof(isycos_mi_out) * n))) return rc;
+    // results, then the sorted path's device-counted work (two counters)
+    const size_t work_off = (sizeof(isycos_mi_out) * (size_t)n + 15) & ~(size_t)15;
+    if ((rc = host_reserve(ctx, L.h_table, work_off + 16))) return rc;
     unsigned char *stage = reinterpret_cast<unsigned char *>(L.h_items.p);
     BucketTable &T = *reinterpret_cast<BucketTable *>(stage);
     build_table(T, count, nt);
@@ -233,7 +235,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     }
     // The work counters are zeroed once; every launch leaves them at zero.
     cudaError_t e = cudaSuccess;
-    if (!L.queue_clean) e = cudaMemsetAsync(L.d_queue.p, 0, 16, st);
+    if (!L.queue_clean) e = cudaMemsetAsync(L.d_queue.p, 0, 128, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_items.p, stage, stage_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "staging the window list");
     L.queue_clean = true;
@@ -265,6 +267,15 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     a.inv_k = est ? 0.0 : 1.0 / (double)k;
     a.gscratch = max_sorted_glob > 0 ? reinterpret_cast<unsigned char *>(L.d_gscratch.p) : nullptr;
     a.gscratch_stride = (int64_t)g_stride;
+    // work counters: device accumulators after the work counters of d_queue
+    a.work = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(L.d_queue.p) + 64);
+    a.work_out = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(L.h_table.dev) + work_off);
+    int64_t work_bf = 0, work_sort = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int m = w[i].m;
+        if (takes_sorted_path(m, nt, smask, a.gscratch != nullptr)) work_sort += sort_cx_steps(m);
+        else work_bf += (int64_t)m * m;
+    }
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(L.ev_stop, st);
@@ -291,6 +302,9 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     o.ny = ny;
     o.c = c;
     o.max_m = max_m;
+    o.work_bf = work_bf;
+    o.work_sort = work_sort;
+    o.work_off = work_off;
     for (int q = 0; q < kBuckets; ++q) o.count[q] = count[q];
     return ISYCOS_OK;
 }
@@ -319,6 +333,12 @@ isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out) {
         const int bmax = kBuckets - 1 - bucket_slot(o.max_m);
         ctx->stats.launches_by_size[bmax] += 1;
         ctx->stats.launch_ms_by_size[bmax] += (double)(t1 - t0);
+        const unsigned long long *wk =
+            reinterpret_cast<const unsigned long long *>(reinterpret_cast<const unsigned char *>(L.h_table.p) + o.work_off);
+        ctx->stats.work_bf += o.work_bf;
+        ctx->stats.work_sort += o.work_sort;
+        ctx->stats.work_scan += (int64_t)wk[0];
+        ctx->stats.work_search += (int64_t)wk[1];
     }
     return ISYCOS_OK;
 }

@@ -61,6 +61,8 @@ struct Lane {
         int32_t *nx = nullptr, *ny = nullptr, *c = nullptr;
         int32_t count[15] = {0};
         int max_m = 0;
+        int64_t work_bf = 0, work_sort = 0;   // known from the sizes
+        size_t work_off = 0;                   // byte offset of the device-counted work in h_table
     } open;
     std::vector<int32_t> h_slot;       // per-call bucket slots (reused)
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;

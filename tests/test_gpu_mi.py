@@ -482,3 +482,49 @@ def test_sorted_path_repeats_bit_exact(ctx):
         api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def _sort_cx(m):
+    lg = 0
+    while (1 << lg) < m:
+        lg += 1
+    return (1 << lg) * lg * (lg + 1) // 2
+
+
+def test_work_counters_follow_the_path_taken(ctx):
+    """The statistics count the work each path really does: m x m point x candidate
+    evaluations per brute-force window; per sorted-path window the compare-exchange steps of
+    its two bitonic sorts (closed form), at least the 48..64 points around every point in the
+    outward scans, and binary-search steps (about five searches of log2 m steps per point)."""
+    api = _api()
+    n = 30000
+    x, y, _ = synth.planted_pair(2, 11, n)
+    xs, ys = api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)
+    sizes = [40, 100, 300, 1025, 2048, 4096]
+    starts = [100 + 4500 * i for i in range(len(sizes))]
+    w = api.windows_array(xs, ys, starts, sizes)
+    try:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 1)
+        api.isycos_reset_stats(ctx)
+        r1 = api.isycos_mi_windows(ctx, w, 4)
+        st = api.isycos_get_stats(ctx)
+        assert st["work_bf"] == sum(m * m for m in sizes)
+        assert st["work_scan"] == st["work_search"] == st["work_sort"] == 0
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 2)
+        api.isycos_reset_stats(ctx)
+        r2 = api.isycos_mi_windows(ctx, w, 4)
+        st = api.isycos_get_stats(ctx)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+    assert np.array_equal(r1, r2)
+    # the launch runs 1024-thread CTAs (its largest sorted window has more than 1024 points):
+    # windows of 257..512 points then run two per CTA, by brute force
+    big = [m for m in sizes if m > 512]
+    assert st["work_bf"] == sum(m * m for m in sizes if m <= 512)
+    assert st["work_sort"] == sum(_sort_cx(m) for m in big)
+    assert st["work_scan"] >= sum(m * 48 for m in big)
+    assert st["work_scan"] < sum(m * m for m in big)
+    lg = {m: int(np.ceil(np.log2(m))) for m in big}
+    assert sum(3 * m * (lg[m] - 2) for m in big) <= st["work_search"] <= sum(6 * m * (lg[m] + 1) for m in big)
+    api.isycos_drop_series(ctx, xs)
+    api.isycos_drop_series(ctx, ys)
