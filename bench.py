@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--length", type=int, default=N_LEN)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-stress", action="store_true", help="skip the noise-pruning stress case")
+    ap.add_argument("--stress-case", action="store_true",
+                    help="run only the noise-pruning stress case and print its JSON")
+    ap.add_argument("--stress-pairs", type=int, default=256)
+    ap.add_argument("--stress-length", type=int, default=200_000)
     ap.add_argument("--kernel-case", default=None,
                     help="time one MI batch instead of the searches: td4096, td1024, td256, "
                          "ring (BU-ring sized windows), mix (all TD layers)")
@@ -78,6 +83,10 @@ def parse():
     ap.add_argument("--serve-series", type=int, default=512)
     ap.add_argument("--serve-length", type=int, default=1_000_000)
     ap.add_argument("--serve-queries", type=int, default=400)
+    ap.add_argument("--serve-calibrate", type=int, default=256,
+                    help="served form in the default run: queries submitted at once to measure capacity")
+    ap.add_argument("--serve-stream", type=int, default=2000,
+                    help="served form in the default run: queries of the Poisson stream")
     ap.add_argument("--serve-rates", default="0.3,0.7,1.0,1.3")
     ap.add_argument("--speculation", type=int, default=-1,
                     help="ISYCOS_OPT_SPECULATION (BU climbs asked ahead; -1: library default)")
@@ -169,68 +178,299 @@ def flush_l2(torch, buf):
     buf.fill_(1.0)          # 256 MiB write, larger than the 129 MB L2
 
 
-def serving_probe(api, ctx, ids, length, n_queries=200, rate_hz=None):
-    """Poisson stream of search queries over the resident pairs (reduced size)."""
-    rng = np.random.default_rng(4)
-    queries = []
-    for i in range(n_queries):
+def _serving_pair(job):
+    """One resident pair of the served workload (config-4 shape); run in a spawned worker."""
+    p, length = job
+    from paper_2204_09131_gb300 import synth
+    x, y, _ = synth.planted_pair(4, p, length)
+    return x, y
+
+
+def put_serving_series(api, ctx, n_pairs, length):
+    """Generate the served pairs in a spawned pool (no CUDA in the workers) and make them
+    resident as they arrive; returns the pairs' series ids."""
+    import multiprocessing as mp
+    ids = []
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        for x, y in pool.imap(_serving_pair, [(p, length) for p in range(n_pairs)], chunksize=2):
+            ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    return ids
+
+
+def serving_queries(ids, length, n, seed):
+    """Random queries over the resident pairs: a random pair, a range log-uniform in
+    [1e3, length], s_max a power of two log-uniform in [256, 16384] clipped to range / 2,
+    SYCOS_TD and SYCOS_BU alternating."""
+    rng = np.random.default_rng(seed)
+    qs = []
+    for i in range(n):
         a, b = ids[int(rng.integers(0, len(ids)))]
         span = int(np.exp(rng.uniform(np.log(1000), np.log(length))))
         lo = int(rng.integers(0, length - span + 1))
-        s_max = int(2 ** rng.integers(8, 13))
+        s_max = int(2 ** rng.integers(8, 15))
         s_max = max(64, min(s_max, span // 2))
-        queries.append((a, b, lo, lo + span, dict(PARAMS, s_max=s_max, mode=int(i % 2))))
-    # calibrate: one query's service time
-    t0 = time.perf_counter()
-    api.isycos_search(ctx, *queries[0][:4], queries[0][4])
-    t1 = time.perf_counter() - t0
-    rate = rate_hz or max(1.0, 0.7 * 32 / max(t1, 1e-4))
-    gaps = rng.exponential(1.0 / rate, n_queries)
-    tickets = []
+        qs.append((a, b, lo, lo + span, dict(PARAMS, s_max=s_max, mode=int(i % 2))))
+    return qs
+
+
+def serve_stream(api, ctx, qs, gaps):
+    """Submit the queries at the given inter-arrival gaps (seconds) while polling the pending
+    ones; returns latencies and admission waits (ms) and the wall time."""
+    pending, lat, wait = [], {}, {}
     start = time.perf_counter()
     nxt = start
-    done = {}
-    for q, g in zip(queries, gaps):
+
+    def drain():
+        still = []
+        for t in pending:
+            r = api.isycos_serve_poll_ex(ctx, t)
+            if r is None:
+                still.append(t)
+            else:
+                lat[t], wait[t] = r[1], r[2]
+        pending[:] = still
+
+    for q, g in zip(qs, gaps):
         nxt += g
         while time.perf_counter() < nxt:
-            for t in tickets:
-                if t not in done:
-                    r = api.isycos_serve_poll(ctx, t)
-                    if r is not None:
-                        done[t] = r[1]
-            time.sleep(0.0005)
-        tickets.append(api.isycos_serve_submit(ctx, *q[:4], q[4]))
-    while len(done) < len(tickets):
-        for t in tickets:
-            if t not in done:
-                r = api.isycos_serve_poll(ctx, t)
-                if r is not None:
-                    done[t] = r[1]
+            drain()
+            time.sleep(0.0002)
+        pending.append(api.isycos_serve_submit(ctx, *q[:4], q[4]))
+    while pending:
+        drain()
         time.sleep(0.0005)
     wall = time.perf_counter() - start
-    lat = np.array([done[t] for t in tickets])
-    return {"queries": n_queries, "arrival_rate_hz": round(rate, 2),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "throughput_qps": round(n_queries / wall, 2)}
+    return np.array(list(lat.values())), np.array(list(wait.values())), wall
 
 
-def cpu_baseline(pairs, budget_s=15.0):
-    """The oracle, single thread, on a bounded sample: TD then BU (pruning on) on prefixes of
-    pair 0 until the CPU budget is spent; evals/s = windows scored / seconds."""
+def serving_config4(args):
+    """The served form at config-4 shape: 512 resident series of 1,000,000 points (256 pairs
+    with planted segments), capacity calibrated by submitting a batch of queries at once, then
+    a Poisson stream at 0.7 x that capacity; p50 / p99 latency, throughput and admission wait."""
+    from paper_2204_09131_gb300 import api
+    n_pairs, length = args.serve_series // 2, args.serve_length
+    ctx = api.isycos_create(0, 0)
+    try:
+        t0 = time.perf_counter()
+        ids = put_serving_series(api, ctx, n_pairs, length)
+        t_put = time.perf_counter() - t0
+        api.isycos_autotune(ctx, PARAMS["k"])
+        cal_q = serving_queries(ids, length, args.serve_calibrate, 1)
+        lat_c, _, wall_c = serve_stream(api, ctx, cal_q, [0.0] * len(cal_q))
+        capacity = len(cal_q) / wall_c
+        qs = serving_queries(ids, length, args.serve_stream, 2)
+        rate = 0.7 * capacity
+        gaps = np.random.default_rng(7).exponential(1.0 / rate, len(qs))
+        lat, wait, wall = serve_stream(api, ctx, qs, gaps)
+        st = api.isycos_get_stats(ctx)
+        return {"workload": "%d resident series x %d points (%d planted pairs); queries: a random "
+                            "pair, range log-uniform 1e3-%d, s_max log-uniform 256-16384 clipped to "
+                            "range/2, SYCOS_TD and SYCOS_BU alternating" % (2 * n_pairs, length, n_pairs, length),
+                "resident_bytes": int(8 * n_pairs * length), "upload_s": round(t_put, 1),
+                "calibration": {"queries": len(cal_q), "submitted": "all at once",
+                                "capacity_qps": round(capacity, 2),
+                                "p50_ms": round(float(np.percentile(lat_c, 50)), 2)},
+                "queries": len(qs), "arrival": "Poisson at 0.7 x capacity",
+                "arrival_rate_hz": round(rate, 2),
+                "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                "throughput_qps": round(len(qs) / wall, 2),
+                "admission_wait_p50_ms": round(float(np.percentile(wait, 50)), 3),
+                "admission_wait_p99_ms": round(float(np.percentile(wait, 99)), 3),
+                "queries_done": st["queries_done"]}
+    finally:
+        api.isycos_destroy(ctx)
+
+
+def _stress_pair(job):
+    """One pair of the noise-pruning stress workload (config-3 shape); run in a spawned worker."""
+    p, length = job
+    from paper_2204_09131_gb300 import synth
+    x, y, _ = synth.planted_pair(3, p, length, len_lo=100, len_hi=10000, background="mixed")
+    return x, y
+
+
+def overlap_agreement(ref, got):
+    """Windows of `ref` that overlap some window of `got` (the paper's accuracy measure of the
+    noise pruning: two windows count as the same when their index ranges overlap)."""
+    hit = 0
+    j = 0
+    got = sorted((int(a), int(b)) for a, b in zip(got["t_s"], got["t_e"]))
+    for a, b in sorted((int(a), int(b)) for a, b in zip(ref["t_s"], ref["t_e"])):
+        while j < len(got) and got[j][1] < a:
+            j += 1
+        if j < len(got) and got[j][0] <= b:
+            hit += 1
+    return hit
+
+
+def pruning_stress(args):
+    """Noise-pruning stress (config-3 shape): --stress-pairs pairs of --stress-length points,
+    70 % independent Gaussian / uniform / Laplace noise and 30 % planted segments of
+    100-10,000 samples; SYCOS_TD and SYCOS_BU of every pair with pruning off and on (k = 4,
+    window sizes 32-8192).  Per mode: decided window-MI evals/s; and the share of the windows
+    found without pruning that overlap a window found with it."""
+    import multiprocessing as mp
+    import torch
+    from paper_2204_09131_gb300 import api
+    n_pairs, length = args.stress_pairs, args.stress_length
+    ctx = api.isycos_create(0, 0)
+    try:
+        ids = []
+        with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            for x, y in pool.imap(_stress_pair, [(p, length) for p in range(n_pairs)], chunksize=2):
+                ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+        api.isycos_autotune(ctx, PARAMS["k"])
+        base = dict(PARAMS, s_max=8192)
+        out = {"workload": "%d pairs x %d points, 70%% independent noise (Gaussian / uniform / Laplace "
+                           "per gap), 30%% planted segments of 100-10000 samples; k=4, sizes 32-8192"
+                           % (n_pairs, length)}
+        res = {}
+        warm = [(a, b, 0, length, dict(base, mode=m, pruning=1)) for a, b in ids[:4] for m in (0, 1)]
+        api.isycos_search_queries(ctx, warm)
+        for pr in (0, 1):
+            qs = [(a, b, 0, length, dict(base, mode=m, pruning=pr)) for m in (0, 1) for a, b in ids]
+            torch.cuda.synchronize()
+            api.isycos_reset_stats(ctx)
+            t0 = time.perf_counter()
+            res[pr] = api.isycos_search_queries(ctx, qs)
+            dt = time.perf_counter() - t0
+            st = api.isycos_get_stats(ctx)
+            out["pruning_%s" % ("on" if pr else "off")] = {
+                "s": round(dt, 3), "decided_windows": st["decided_windows"],
+                "evals_per_s": round(st["decided_windows"] / dt, 1),
+                "gpu_windows": st["windows"], "found": int(sum(len(r) for r in res[pr]))}
+        for name, sl in (("td", slice(0, n_pairs)), ("bu", slice(n_pairs, 2 * n_pairs))):
+            ref = res[0][sl]
+            hit = sum(overlap_agreement(r, g) for r, g in zip(ref, res[1][sl]))
+            tot = sum(len(r) for r in ref)
+            out["agreement_" + name] = {"found_without_pruning": tot, "overlapped_with_pruning": hit,
+                                        "fraction": round(hit / tot, 4) if tot else None}
+        out["speedup_of_pruning"] = round(out["pruning_off"]["s"] / out["pruning_on"]["s"], 2)
+        return out
+    finally:
+        api.isycos_destroy(ctx)
+
+
+def host_info():
+    """The host the oracle runs on: cores it may use and the CPU model."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"nproc": os.cpu_count(), "usable_cores": usable,
+            "cpu_model": model or platform.machine()}
+
+
+# windows per size bucket b (2^(b-1) < m <= 2^b) of the oracle's timing sample
+_BUCKET_SAMPLE = {3: 400, 4: 400, 5: 300, 6: 200, 7: 100, 8: 40, 9: 16, 10: 8, 11: 4, 12: 3, 13: 2, 14: 1}
+
+
+def oracle_bucket_cost(x, y, k=4, seed=9):
+    """Seconds the oracle (one core) takes per window of each size bucket, on a seeded sample
+    of windows of the pair (x, y)."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    n = len(x)
+    cost = {}
+    for b, cnt in _BUCKET_SAMPLE.items():
+        lo, hi = max(k + 1, (1 << (b - 1)) + 1), 1 << b
+        if lo > hi or hi > n:
+            continue
+        wins = []
+        for _ in range(cnt):
+            m = int(rng.integers(lo, hi + 1))
+            st = int(rng.integers(0, n - m + 1))
+            wins.append((st, m))
+        t0 = time.perf_counter()
+        for st, m in wins:
+            O.ksg_window(x[st:st + m], y[st:st + m], k, points=False)
+        cost[b] = (time.perf_counter() - t0) / cnt
+    return cost
+
+
+def config1_full():
+    """Config 1 in full on the oracle: every window of 32, 64 and 128 points at stride 1 of the
+    n = 2000 planted pair, and SYCOS_TD / SYCOS_BU with pruning off and on (sizes 32-256)."""
+    from oracle import oracle as O
+    from paper_2204_09131_gb300 import synth
+    x, y = synth.planted_small_pair()
+    wins = synth.stride_windows(len(x), [32, 64, 128])
+    t0 = time.perf_counter()
+    for st, m in wins:
+        O.ksg_window(x[st:st + m], y[st:st + m], 4, points=False)
+    t_sweep = time.perf_counter() - t0
+    searches = {}
+    for name, fn in (("td", O.search_td), ("bu", O.search_bu)):
+        for pr in (0, 1):
+            t0 = time.perf_counter()
+            found, n_ev = fn(x, y, k=4, s_min=32, s_max=256, sigma=0.2, pruning=pr, seed=11)
+            dt = time.perf_counter() - t0
+            searches["%s_pruning%d" % (name, pr)] = {"evals": n_ev, "s": round(dt, 3),
+                                                     "found": len(found)}
+    return {"sweep_windows": len(wins), "sweep_s": round(t_sweep, 3),
+            "sweep_evals_per_s": round(len(wins) / t_sweep, 1), "searches": searches}
+
+
+def cpu_baseline(pairs, decided_by_size=None, steps=1, prefix=12000):
+    """The oracle, single thread, on bounded samples of the workload.
+
+    value: the step's decided windows divided by the oracle's extrapolated time for them --
+    per size bucket, the oracle's mean seconds per window on a seeded sample of the pair's
+    windows, times the step's decided windows in that bucket (labelled "extrapolated").
+    Beside it: the oracle's SYCOS_TD + SYCOS_BU measured on the first `prefix` points of pair
+    0 (real searches, also compared with the GPU's), and config 1 timed in full."""
     from oracle import oracle as O
     x, y = pairs[0]
+    out = {"unit": "evals/s", "cores": 1, "kind": "oracle", "host": host_info()}
+    cost = oracle_bucket_cost(x, y)
+    out["per_bucket_s"] = {b: round(c, 7) for b, c in cost.items()}
     kw = dict(PARAMS)
-    evals, secs = 0, 0.0
-    span = 12000
     t0 = time.perf_counter()
-    _, n1 = O.search_td(x[:span], y[:span], **kw)
-    _, n2 = O.search_bu(x[:span], y[:span], **kw)
+    td, n1 = O.search_td(x[:prefix], y[:prefix], **kw)
+    bu, n2 = O.search_bu(x[:prefix], y[:prefix], **kw)
     secs = time.perf_counter() - t0
-    evals = n1 + n2
-    return {"value": round(evals / secs, 2), "unit": "evals/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first "
-                      "%d points of pair 0: %d window scores in %.1f s" % (span, evals, secs)}
+    out["measured_search"] = {"value": round((n1 + n2) / secs, 2), "evals": n1 + n2, "s": round(secs, 2),
+                              "sample": "SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the "
+                                        "first %d points of pair 0" % prefix}
+    out["_searches"] = (td, bu)
+    if decided_by_size is not None:
+        per_step = [v / steps for v in decided_by_size]
+        missing = [b for b, v in enumerate(per_step) if v > 0 and b not in cost]
+        t_step = sum(v * cost.get(b, 0.0) for b, v in enumerate(per_step))
+        out["value"] = round(sum(per_step) / t_step, 2) if t_step > 0 else None
+        out["extrapolated"] = True
+        out["extrapolated_s_per_step"] = round(t_step, 1)
+        out["sample"] = ("extrapolated: the oracle's seconds per window by size bucket (seeded sample "
+                         "of %d windows of pair 0, sizes 5-16384) x the step's decided windows per "
+                         "bucket" % sum(_BUCKET_SAMPLE.values()))
+        if missing:
+            out["buckets_without_sample"] = missing
+    else:
+        out["value"] = out["measured_search"]["value"]
+        out["sample"] = "oracle " + out["measured_search"]["sample"]
+    out["config1_full"] = config1_full()
+    return out
 
 
 def reference_arm(args):
@@ -238,12 +478,26 @@ def reference_arm(args):
     if rank != 0:
         return
     pairs = make_pairs(0, 1, args.length)
+    x, y = pairs[0]
+
+    def one_step():
+        """The oracle's SYCOS_TD + SYCOS_BU on the first 12,000 points of pair 0."""
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        _, n1 = O.search_td(x[:12000], y[:12000], **PARAMS)
+        _, n2 = O.search_bu(x[:12000], y[:12000], **PARAMS)
+        dt = time.perf_counter() - t0
+        return {"value": round((n1 + n2) / dt, 2), "unit": "evals/s", "cores": 1, "kind": "oracle",
+                "host": host_info(),
+                "sample": "oracle SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first "
+                          "12000 points of pair 0: %d window scores in %.1f s" % (n1 + n2, dt)}
+
     for _ in range(args.warmup):   # untimed, like the other arm's warm-up steps
-        cpu_baseline(pairs)
+        one_step()
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(pairs))
+        vals.append(one_step())
     ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     v = statistics.median([c["value"] for c in vals])
     line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
@@ -411,78 +665,35 @@ def search_case(args):
 
 
 def serving_case(args):
-    """Continuous batching at scale: random queries (random pair of the resident series, range
-    log-uniform in [1e3, length], s_max a power of two log-uniform in [256, 16384] clipped to
-    range / 2, SYCOS_TD and SYCOS_BU alternating) submitted as Poisson streams at fractions
-    of the capacity measured with the same kind of queries submitted all at once."""
+    """Continuous batching at scale, swept over load: --serve-series resident series of
+    --serve-length points, capacity measured with --serve-calibrate queries submitted at once,
+    then Poisson streams of --serve-queries queries at the fractions --serve-rates of it."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2204_09131_gb300 import api, synth
+    from paper_2204_09131_gb300 import api
     ctx = api.isycos_create(0, 0)
-    n_pairs = max(1, args.serve_series // 2)
-    ids = []
-    for p in range(n_pairs):
-        x, y, _ = synth.planted_pair(4, p, args.serve_length)
-        ids.append((api.isycos_put_series(ctx, x), api.isycos_put_series(ctx, y)))
+    n_pairs, length = max(1, args.serve_series // 2), args.serve_length
+    ids = put_serving_series(api, ctx, n_pairs, length)
     api.isycos_autotune(ctx, PARAMS["k"])
-    length = args.serve_length
-
-    def make_queries(n, seed):
-        rng = np.random.default_rng(seed)
-        qs = []
-        for i in range(n):
-            a, b = ids[int(rng.integers(0, len(ids)))]
-            span = int(np.exp(rng.uniform(np.log(1000), np.log(length))))
-            lo = int(rng.integers(0, length - span + 1))
-            s_max = int(2 ** rng.integers(8, 15))
-            s_max = max(64, min(s_max, span // 2))
-            qs.append((a, b, lo, lo + span, dict(PARAMS, s_max=s_max, mode=int(i % 2))))
-        return qs
-
-    def run(qs, gaps):
-        tickets, done = [], {}
-        start = time.perf_counter()
-        nxt = start
-        for q, g in zip(qs, gaps):
-            nxt += g
-            while time.perf_counter() < nxt:
-                time.sleep(0.0002)
-            tickets.append(api.isycos_serve_submit(ctx, *q[:4], q[4]))
-            for t in tickets[-64:]:
-                if t not in done:
-                    r = api.isycos_serve_poll(ctx, t)
-                    if r is not None:
-                        done[t] = r[1]
-        while len(done) < len(tickets):
-            for t in tickets:
-                if t not in done:
-                    r = api.isycos_serve_poll(ctx, t)
-                    if r is not None:
-                        done[t] = r[1]
-            time.sleep(0.001)
-        wall = time.perf_counter() - start
-        lat = np.array([done[t] for t in tickets])
-        return {"queries": len(qs), "p50_ms": round(float(np.percentile(lat, 50)), 2),
-                "p99_ms": round(float(np.percentile(lat, 99)), 2),
-                "throughput_qps": round(len(qs) / wall, 2)}
-
-    cal = run(make_queries(min(256, args.serve_queries), 1), [0.0] * min(256, args.serve_queries))
-    capacity = cal["throughput_qps"]
+    cal_q = serving_queries(ids, length, args.serve_calibrate, 1)
+    _, _, wall = serve_stream(api, ctx, cal_q, [0.0] * len(cal_q))
+    capacity = len(cal_q) / wall
     sweep = []
     for f in [float(v) for v in args.serve_rates.split(",")]:
-        qs = make_queries(args.serve_queries, 100 + int(f * 100))
+        qs = serving_queries(ids, length, args.serve_queries, 100 + int(f * 100))
         gaps = np.random.default_rng(7).exponential(1.0 / (f * capacity), len(qs))
-        r = run(qs, gaps)
-        r["rate_fraction"] = f
-        r["arrival_qps"] = round(f * capacity, 2)
-        sweep.append(r)
+        lat, wait, wall = serve_stream(api, ctx, qs, gaps)
+        sweep.append({"rate_fraction": f, "arrival_qps": round(f * capacity, 2), "queries": len(qs),
+                      "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                      "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                      "throughput_qps": round(len(qs) / wall, 2),
+                      "admission_wait_p99_ms": round(float(np.percentile(wait, 99)), 3)})
     st = api.isycos_get_stats(ctx)
-    line = {"serving_case": True, "series": 2 * n_pairs, "length": length,
-            "capacity_qps": capacity, "calibration": cal, "sweep": sweep,
-            "queries_done": st["queries_done"]}
-    print(json.dumps(line), flush=True)
+    print(json.dumps({"serving_case": True, "series": 2 * n_pairs, "length": length,
+                      "capacity_qps": round(capacity, 2), "sweep": sweep,
+                      "queries_done": st["queries_done"]}), flush=True)
     api.isycos_destroy(ctx)
 
 
@@ -496,6 +707,13 @@ def main():
         return reference_arm(args)
     if args.kernel_case:
         return kernel_case(args)
+    if args.stress_case:
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(pruning_stress(args)), flush=True)
+        return
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -607,7 +825,10 @@ def main():
 
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = serving_probe(api, ctx, ids, args.length)
+        serving = serving_config4(args)
+    stress = None
+    if rank == 0 and not args.no_stress:
+        stress = pruning_stress(args)
 
     # the plain form (one window per launch) against the batched form, on 2,000 windows shaped
     # like the BU rings of the step (32-1024 points)
@@ -632,7 +853,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pairs)
+        cpu = cpu_baseline(pairs, st["decided_by_size"], args.steps)
+        # the GPU's searches on the same prefix must return the oracle's windows
+        td, bu = cpu.pop("_searches")
+        got = api.isycos_search_queries(ctx, [(ids[0][0], ids[0][1], 0, 12000, dict(PARAMS, mode=0)),
+                                              (ids[0][0], ids[0][1], 0, 12000, dict(PARAMS, mode=1))])
+        same = all([(int(a), int(b)) for a, b in zip(g["t_s"], g["t_e"])] == [(a, b) for a, b, _, _ in r]
+                   for g, r in ((got[0], td), (got[1], bu)))
+        cpu["measured_search"]["gpu_same_windows"] = bool(same)
 
     if rank == 0:
         line = {
@@ -657,7 +885,7 @@ def main():
             "incremental_windows_per_step": int(st["incr_windows"] / args.steps),
             "gpu_launches": int(st["launches"]),
             "roofline": roof, "clocks": clocks, "e2e": e2e, "serving": serving,
-            "plain_vs_batched": plain,
+            "plain_vs_batched": plain, "pruning_stress": stress,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

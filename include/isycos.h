@@ -307,6 +307,13 @@ isycos_status isycos_serve_submit(isycos_ctx *ctx, int32_t xs, int32_t ys, int64
 isycos_status isycos_serve_poll(isycos_ctx *ctx, uint64_t ticket, isycos_result_window *out,
                                 int64_t cap, int64_t *n_out, double *latency_ms);
 
+/* As isycos_serve_poll, also returning the query's admission wait: the milliseconds from
+ * submission until a slot and device memory were free and the query joined the running
+ * ones (wait_ms may be NULL). */
+isycos_status isycos_serve_poll_ex(isycos_ctx *ctx, uint64_t ticket, isycos_result_window *out,
+                                   int64_t cap, int64_t *n_out, double *latency_ms,
+                                   double *wait_ms);
+
 /* Cancel a queued or running query; a later poll returns E_CANCELED. */
 isycos_status isycos_serve_cancel(isycos_ctx *ctx, uint64_t ticket);
 

@@ -135,6 +135,8 @@ SIGNATURES = {
                                    ctypes.POINTER(_U64)]),
     "isycos_serve_poll": (_I32, [_VP, _U64, _VP, _I64, ctypes.POINTER(_I64),
                                  ctypes.POINTER(ctypes.c_double)]),
+    "isycos_serve_poll_ex": (_I32, [_VP, _U64, _VP, _I64, ctypes.POINTER(_I64),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "isycos_serve_cancel": (_I32, [_VP, _U64]),
     "isycos_get_stats": (_I32, [_VP, ctypes.POINTER(isycos_stats)]),
     "isycos_reset_stats": (_I32, [_VP]),
@@ -351,6 +353,24 @@ def isycos_serve_submit(ctx, xs: int, ys: int, t_begin: int, t_end: int, params=
     _check(ctx, lib().isycos_serve_submit(ctx, xs, ys, t_begin, t_end, ctypes.byref(p),
                                           ctypes.byref(t)))
     return t.value
+
+
+def isycos_serve_poll_ex(ctx, ticket: int, cap: int = 1024):
+    """Returns None while pending, else (windows, latency_ms, admission_wait_ms)."""
+    while True:
+        out = np.empty(cap, dtype=RESULT_DTYPE)
+        n = ctypes.c_int64()
+        lat = ctypes.c_double()
+        wait = ctypes.c_double()
+        st = lib().isycos_serve_poll_ex(ctx, ticket, _ptr(out), cap, ctypes.byref(n), ctypes.byref(lat),
+                                        ctypes.byref(wait))
+        if st == PENDING:
+            return None
+        if st == E_TRUNC and n.value > cap:
+            cap = int(n.value)
+            continue
+        _check(ctx, st)
+        return out[:n.value].copy(), lat.value, wait.value
 
 
 def isycos_serve_poll(ctx, ticket: int, cap: int = 1024):

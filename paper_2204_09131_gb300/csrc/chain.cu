@@ -272,6 +272,7 @@ cudaError_t launch_chain(const ChainArgs &a, int n_chains, int max_cap, cudaStre
     const size_t smem = chain_smem(max_cap);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    (void)cudaGetLastError();   // (an error left by an earlier call is not this launch's)
     fn<<<n_chains, kChainThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -388,7 +389,9 @@ isycos_status engine_eval_chains(isycos_ctx *ctx, Lane &L, const ChainSpec *spec
     a.recomputed = reinterpret_cast<int32_t *>(L.d_chain_recomp.p);
     a.k = k;
     e = launch_chain(a, (int)chains.size(), max_cap, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "chain kernel launch");
+    if (e != cudaSuccess)
+        return fail(ctx, ISYCOS_E_CUDA, "chain kernel launch (%d chains, ring of %d points, %zu bytes of shared memory): %s",
+                    (int)chains.size(), max_cap, chain_smem(max_cap), cudaGetErrorString(e));
     std::vector<int32_t> recomp((size_t)n_out + 1);
     std::vector<isycos_mi_out> all((size_t)n_out + 1);
     e = cudaMemcpyAsync(all.data(), L.d_chain_out.p, sizeof(isycos_mi_out) * (n_out + 1),

@@ -75,7 +75,7 @@ public:
     }
 
     isycos_status poll(uint64_t ticket, isycos_result_window *out, int64_t cap, int64_t *n_out,
-                       double *latency_ms) {
+                       double *latency_ms, double *wait_ms = nullptr) {
         std::lock_guard<std::mutex> g(mu_);
         auto it = all_.find(ticket);
         if (it == all_.end()) return fail(ctx_, ISYCOS_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
@@ -92,6 +92,7 @@ public:
         }
         if (n_out) *n_out = (int64_t)q.result.size();
         if (latency_ms) *latency_ms = q.latency_ms;
+        if (wait_ms) *wait_ms = q.wait_ms;
         if ((int64_t)q.result.size() > cap || (!out && !q.result.empty()))
             return fail(ctx_, ISYCOS_E_TRUNC, "query %llu found %lld windows, capacity %lld",
                         (unsigned long long)ticket, (long long)q.result.size(), (long long)cap);
@@ -127,6 +128,7 @@ private:
         SearchParams prm{};
         std::unique_ptr<SearchMachine> sm;
         Clock::time_point t_submit;
+        double wait_ms = 0.0;   // from submission to admission
         State state = kQueued;
         bool cancel = false;
         std::vector<isycos_result_window> result;
@@ -181,6 +183,7 @@ private:
             queue_.pop_front();
             q.sm = make_machine(q.xs, q.ys, q.tb, q.te, q.prm);
             q.state = kRunning;
+            q.wait_ms = std::chrono::duration<double, std::milli>(Clock::now() - q.t_submit).count();
             reserved_ += q.bytes;
             size_t w = 0;
             for (size_t i = 1; i < running_.size(); ++i)
@@ -319,6 +322,13 @@ isycos_status isycos_serve_poll(isycos_ctx *ctx, uint64_t ticket, isycos_result_
                                 int64_t cap, int64_t *n_out, double *latency_ms) {
     if (!ctx) return ISYCOS_E_INVAL;
     return get_server(ctx)->poll(ticket, out, cap, n_out, latency_ms);
+}
+
+isycos_status isycos_serve_poll_ex(isycos_ctx *ctx, uint64_t ticket, isycos_result_window *out,
+                                   int64_t cap, int64_t *n_out, double *latency_ms,
+                                   double *wait_ms) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    return get_server(ctx)->poll(ticket, out, cap, n_out, latency_ms, wait_ms);
 }
 
 isycos_status isycos_serve_cancel(isycos_ctx *ctx, uint64_t ticket) {
