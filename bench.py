@@ -780,9 +780,8 @@ def main():
         pinned = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()) for x, y in pairs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        eids = []
-        for x, y in pinned:
-            eids.append((api.isycos_put_series(ctx, x.numpy()), api.isycos_put_series(ctx, y.numpy())))
+        flat = api.isycos_put_series_many(ctx, [t.numpy() for xy in pinned for t in xy])
+        eids = list(zip(flat[0::2], flat[1::2]))
         st0 = api.isycos_get_stats(ctx)
         nfound = run_step(api, ctx, eids, args.length)
         st1 = api.isycos_get_stats(ctx)

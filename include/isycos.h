@@ -188,7 +188,18 @@ void isycos_params_default(isycos_params *p);
 isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n,
                                 int32_t on_device, int32_t *series_id);
 
-/* Release a resident series.  Errors: E_NOTFOUND. */
+/* Make count series resident in one call: series s is data[s][0 .. n[s] - 1] (device memory
+ * if on_device != 0, else host memory); series_ids[s] receives its id.  The copies are
+ * queued together and the call synchronises once (isycos_put_series synchronises per
+ * series).  Same checks and errors as isycos_put_series; on any error no series of the call
+ * is made resident. */
+isycos_status isycos_put_series_many(isycos_ctx *ctx, int32_t count, const float *const *data,
+                                     const int64_t *n, int32_t on_device, int32_t *series_ids);
+
+/* Release a resident series.  Its device memory is kept by the context for a later series of
+ * about its size (so that a put / drop cycle allocates nothing), and freed by isycos_destroy
+ * or when the context's budget needs it.  A call still reading the series must have
+ * completed (every synchronous call has).  Errors: E_NOTFOUND. */
 isycos_status isycos_drop_series(isycos_ctx *ctx, int32_t series_id);
 
 /* Device address and length of a resident series (read-only for the caller). */

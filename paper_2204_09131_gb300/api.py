@@ -118,6 +118,7 @@ SIGNATURES = {
     "isycos_last_error": (ctypes.c_char_p, [_VP]),
     "isycos_params_default": (None, [ctypes.POINTER(isycos_params)]),
     "isycos_put_series": (_I32, [_VP, _VP, _I64, _I32, ctypes.POINTER(_I32)]),
+    "isycos_put_series_many": (_I32, [_VP, _I32, _VP, _VP, _I32, _VP]),
     "isycos_drop_series": (_I32, [_VP, _I32]),
     "isycos_series_info": (_I32, [_VP, _I32, ctypes.POINTER(_VP), ctypes.POINTER(_I64)]),
     "isycos_mi_windows": (_I32, [_VP, _VP, _I64, _I32, _VP, _VP]),
@@ -230,6 +231,33 @@ def isycos_put_series(ctx, data) -> int:
         on_dev, n, p = 0, data.shape[0], data.ctypes.data
     _check(ctx, lib().isycos_put_series(ctx, p, n, on_dev, ctypes.byref(sid)))
     return sid.value
+
+
+def isycos_put_series_many(ctx, arrays) -> list:
+    """Make several series resident in one call (one synchronisation): float32 NumPy arrays
+    (host) or torch CUDA tensors (device), all of the same kind."""
+    keep, ptrs, ns, kinds = [], [], [], set()
+    for a in arrays:
+        if hasattr(a, "data_ptr"):
+            assert a.dtype.__str__() == "torch.float32" and a.is_contiguous()
+            kinds.add(1 if a.is_cuda else 0)
+            ptrs.append(a.data_ptr())
+            ns.append(a.numel())
+        else:
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            kinds.add(0)
+            ptrs.append(a.ctypes.data)
+            ns.append(a.shape[0])
+        keep.append(a)
+    if not ptrs:
+        return []
+    assert len(kinds) == 1, "all series in host memory or all on the device"
+    p = np.array(ptrs, dtype=np.uint64)
+    n = np.array(ns, dtype=np.int64)
+    ids = np.zeros(len(ptrs), dtype=np.int32)
+    _check(ctx, lib().isycos_put_series_many(ctx, len(ptrs), p.ctypes.data, n.ctypes.data, kinds.pop(),
+                                             ids.ctypes.data))
+    return [int(v) for v in ids]
 
 
 def isycos_drop_series(ctx, sid: int):

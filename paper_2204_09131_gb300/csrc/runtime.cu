@@ -553,6 +553,8 @@ isycos_status isycos_destroy(isycos_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (float *p : ctx->series_ptr)
         if (p) cudaFree(p);
+    for (auto &kv : ctx->series_pool) cudaFree(kv.second);
+    ctx->series_pool.clear();
     for (int i = 0; i < kLaneSlots; ++i) {
         Lane *L = ctx->lanes[i].exchange(nullptr);
         if (!L) continue;
@@ -600,69 +602,133 @@ static int64_t first_nonfinite(const float *d, int64_t n) {
     return -1;
 }
 
-isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, int32_t on_device,
-                                int32_t *series_id) {
-    if (!ctx) return ISYCOS_E_INVAL;
-    if (!data || n < 1 || !series_id) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments");
+// Device memory for a series of `bytes`: a buffer kept from a dropped series when one of
+// between `bytes` and twice that is free, else a new allocation (buffers kept from dropped
+// series are freed first when the budget or the device runs short).  Caller holds engine_mu.
+static isycos_status series_alloc(isycos_ctx *ctx, size_t bytes, float **out, size_t *cap) {
+    auto it = ctx->series_pool.lower_bound(bytes);
+    if (it != ctx->series_pool.end() && it->first <= 2 * bytes) {
+        *out = it->second;
+        *cap = it->first;
+        ctx->series_pool.erase(it);
+        return ISYCOS_OK;
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (ctx->used.load() + bytes <= ctx->budget) {
+            float *d = nullptr;
+            if (cudaMalloc(&d, bytes) == cudaSuccess) {
+                ctx->used += bytes;
+                ctx->series_bytes += bytes;
+                *out = d;
+                *cap = bytes;
+                return ISYCOS_OK;
+            }
+            cudaGetLastError();
+        }
+        if (ctx->series_pool.empty()) break;
+        for (auto &kv : ctx->series_pool) {   // give the kept buffers back and try again
+            cudaFree(kv.second);
+            ctx->used -= kv.first;
+            ctx->series_bytes -= kv.first;
+        }
+        ctx->series_pool.clear();
+    }
+    return fail(ctx, ISYCOS_E_NOMEM, "put_series: no device memory for %zu bytes within the budget", bytes);
+}
+
+static void series_release(isycos_ctx *ctx, float *d, size_t cap) {
+    ctx->series_pool.emplace(cap, d);
+}
+
+// Make `count` series resident: one copy each on the context's stream, one device-side
+// finiteness check over the series given in device memory, one synchronisation.  On any
+// error nothing is made resident.
+static isycos_status put_series_list(isycos_ctx *ctx, int32_t count, const float *const *data,
+                                     const int64_t *n, int32_t on_device, int32_t *ids) {
+    if (count < 0 || (count > 0 && (!data || !n || !ids))) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments");
+    for (int32_t s = 0; s < count; ++s)
+        if (!data[s] || n[s] < 1) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments (series %d)", s);
     std::lock_guard<std::mutex> g(ctx->engine_mu);
     cudaSetDevice(ctx->device);
-    const size_t bytes = sizeof(float) * (size_t)n;
-    if (!on_device) {
-        const int64_t i = first_nonfinite(data, n);
-        if (i >= 0) return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld is not finite", (long long)i);
-    }
-    if (ctx->used.load() + bytes > ctx->budget)
-        return fail(ctx, ISYCOS_E_NOMEM, "put_series: device budget exceeded");
-    float *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, ISYCOS_E_NOMEM, "put_series: cudaMalloc(%zu) failed", bytes);
-    }
-    ctx->used += bytes;
-    e = cudaMemcpyAsync(d, data, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                        ctx->stream);
+    if (!on_device)
+        for (int32_t s = 0; s < count; ++s) {
+            const int64_t i = first_nonfinite(data[s], n[s]);
+            if (i >= 0)
+                return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld of series %d is not finite", (long long)i, s);
+        }
+    size_t free_slots = 0;
+    for (float *p : ctx->series_ptr) free_slots += p ? 0 : 1;
+    if (ctx->series_ptr.size() - free_slots + (size_t)count > (size_t)kMaxSeries)
+        return fail(ctx, ISYCOS_E_NOMEM, "put_series: at most %d series resident", kMaxSeries);
+    std::vector<float *> dev((size_t)count, nullptr);
+    std::vector<size_t> caps((size_t)count, 0);
+    auto undo = [&](int32_t upto) {
+        for (int32_t s = 0; s < upto; ++s) series_release(ctx, dev[s], caps[s]);
+    };
+    isycos_status rc;
+    for (int32_t s = 0; s < count; ++s)
+        if ((rc = series_alloc(ctx, sizeof(float) * (size_t)n[s], &dev[s], &caps[s]))) {
+            undo(s);
+            return rc;
+        }
+    cudaError_t e = cudaSuccess;
+    for (int32_t s = 0; s < count && e == cudaSuccess; ++s)
+        e = cudaMemcpyAsync(dev[s], data[s], sizeof(float) * (size_t)n[s],
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
     int32_t bad = 0;
     if (e == cudaSuccess && on_device) {
-        isycos_status rc = dev_reserve(ctx, ctx->d_status, 256);
-        if (rc) {
-            cudaFree(d);
-            ctx->used -= bytes;
+        if ((rc = dev_reserve(ctx, ctx->d_status, 256))) {
+            cudaStreamSynchronize(ctx->stream);
+            undo(count);
             return rc;
         }
         int32_t *flag = reinterpret_cast<int32_t *>(ctx->d_status.p) + 8;
         e = cudaMemsetAsync(flag, 0, 4, ctx->stream);
-        if (e == cudaSuccess) e = launch_check_finite(d, n, flag, ctx->stream);
+        for (int32_t s = 0; s < count && e == cudaSuccess; ++s) e = launch_check_finite(dev[s], n[s], flag, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, ctx->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess || bad) {
-        cudaFree(d);
-        ctx->used -= bytes;
+        cudaStreamSynchronize(ctx->stream);
+        undo(count);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "put_series");
-        return fail(ctx, ISYCOS_E_INVAL, "put_series: the series holds non-finite values");
+        return fail(ctx, ISYCOS_E_INVAL, "put_series: a series holds non-finite values");
     }
-    int32_t id = -1;
-    for (size_t i = 0; i < ctx->series_ptr.size(); ++i)
-        if (!ctx->series_ptr[i]) {
-            id = (int32_t)i;
-            break;
+    size_t scan = 0;
+    for (int32_t s = 0; s < count; ++s) {
+        int32_t id = -1;
+        for (; scan < ctx->series_ptr.size(); ++scan)
+            if (!ctx->series_ptr[scan]) {
+                id = (int32_t)scan++;
+                break;
+            }
+        if (id < 0) {
+            id = (int32_t)ctx->series_ptr.size();
+            ctx->series_ptr.push_back(nullptr);
+            ctx->series_len.push_back(0);
+            ctx->series_cap.push_back(0);
+            scan = ctx->series_ptr.size();
         }
-    if (id < 0) {
-        if (ctx->series_ptr.size() >= (size_t)kMaxSeries) {
-            cudaFree(d);
-            ctx->used -= bytes;
-            return fail(ctx, ISYCOS_E_NOMEM, "put_series: %d series resident", kMaxSeries);
-        }
-        id = (int32_t)ctx->series_ptr.size();
-        ctx->series_ptr.push_back(nullptr);
-        ctx->series_len.push_back(0);
+        ctx->series_ptr[id] = dev[s];
+        ctx->series_len[id] = n[s];
+        ctx->series_cap[id] = caps[s];
+        ids[s] = id;
     }
-    ctx->series_ptr[id] = d;
-    ctx->series_len[id] = n;
     ctx->series_dirty = true;
-    *series_id = id;
     return ISYCOS_OK;
+}
+
+isycos_status isycos_put_series(isycos_ctx *ctx, const float *data, int64_t n, int32_t on_device,
+                                int32_t *series_id) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    if (!data || n < 1 || !series_id) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments");
+    return put_series_list(ctx, 1, &data, &n, on_device, series_id);
+}
+
+isycos_status isycos_put_series_many(isycos_ctx *ctx, int32_t count, const float *const *data,
+                                     const int64_t *n, int32_t on_device, int32_t *series_ids) {
+    if (!ctx) return ISYCOS_E_INVAL;
+    return put_series_list(ctx, count, data, n, on_device, series_ids);
 }
 
 isycos_status isycos_drop_series(isycos_ctx *ctx, int32_t series_id) {
@@ -672,10 +738,11 @@ isycos_status isycos_drop_series(isycos_ctx *ctx, int32_t series_id) {
         return fail(ctx, ISYCOS_E_NOTFOUND, "unknown series %d", series_id);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->series_ptr[series_id]);
-    ctx->used -= sizeof(float) * (size_t)ctx->series_len[series_id];
+    // the memory is kept for the next series of about its size
+    series_release(ctx, ctx->series_ptr[series_id], ctx->series_cap[series_id]);
     ctx->series_ptr[series_id] = nullptr;
     ctx->series_len[series_id] = 0;
+    ctx->series_cap[series_id] = 0;
     ctx->series_dirty = true;
     return ISYCOS_OK;
 }

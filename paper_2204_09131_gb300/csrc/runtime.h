@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -93,6 +94,10 @@ struct isycos_ctx {
     // Resident series.
     std::vector<float *> series_ptr;
     std::vector<int64_t> series_len;
+    std::vector<size_t> series_cap;                  // bytes allocated for each series
+    std::multimap<size_t, float *> series_pool;      // buffers of dropped series, by bytes
+    std::atomic<uint64_t> series_bytes{0};           // device bytes of all series buffers
+                                                     // (resident and kept), read by serving
     isy::DevBuf d_series_ptr, d_series_len;
     bool series_dirty = true;
 

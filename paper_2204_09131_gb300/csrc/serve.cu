@@ -155,10 +155,8 @@ private:
     }
 
     size_t capacity() const {
-        size_t series = 0;
-        for (size_t i = 0; i < ctx_->series_len.size(); ++i)
-            if (ctx_->series_ptr[i]) series += sizeof(float) * (size_t)ctx_->series_len[i];
-        const size_t fixed = series + 2 * sizeof(long long) * kTableN;
+        // (an atomic total: the series tables may grow under another thread meanwhile)
+        const size_t fixed = (size_t)ctx_->series_bytes.load() + 2 * sizeof(long long) * kTableN;
         return ctx_->budget > fixed ? ctx_->budget - fixed : 0;
     }
 

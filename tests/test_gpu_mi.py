@@ -528,3 +528,39 @@ def test_work_counters_follow_the_path_taken(ctx):
     assert sum(3 * m * (lg[m] - 2) for m in big) <= st["work_search"] <= sum(6 * m * (lg[m] + 1) for m in big)
     api.isycos_drop_series(ctx, xs)
     api.isycos_drop_series(ctx, ys)
+
+
+def test_put_series_many_and_reuse_of_dropped_memory(ctx):
+    """isycos_put_series_many makes several series resident with one synchronisation; a
+    batch holding a non-finite value makes none resident; dropped series leave their memory
+    to the next series of about their size, so a put / drop cycle allocates nothing."""
+    import torch
+    api = _api()
+    n = 50000
+    pairs = [synth.planted_pair(2, 20 + p, n)[:2] for p in range(4)]
+    flat = api.isycos_put_series_many(ctx, [a for xy in pairs for a in xy])
+    assert len(set(flat)) == 8
+    w = api.windows_array(flat[0], flat[1], [0, 1000, 30000], [64, 700, 4096])
+    ref = api.isycos_mi_windows(ctx, w, 4)
+    bad = [pairs[0][0].copy(), pairs[0][1].copy()]
+    bad[1][17] = np.inf
+    with pytest.raises(api.IsycosError) as e:
+        api.isycos_put_series_many(ctx, bad)
+    assert e.value.status == api.E_INVAL
+    for sid in flat:
+        api.isycos_drop_series(ctx, sid)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for rep in range(3):   # the same sizes again: the kept buffers serve them
+        dev = [torch.from_numpy(a).cuda() for xy in pairs for a in xy]
+        torch.cuda.synchronize()
+        free_t, _ = torch.cuda.mem_get_info()
+        ids = api.isycos_put_series_many(ctx, dev)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free_t, (rep, free_t, free1)
+        got = api.isycos_mi_windows(ctx, api.windows_array(ids[0], ids[1], [0, 1000, 30000], [64, 700, 4096]), 4)
+        assert np.array_equal(got, ref)
+        for sid in ids:
+            api.isycos_drop_series(ctx, sid)
+        del dev
