@@ -717,8 +717,7 @@ __device__ void load_tile(Shared &S, const DevBuQuery &q, long long lo, long lon
     long long base = max((long long)q.t_begin, lo - 256);
     if (base + kBuTile > q.t_end) base = max((long long)q.t_begin, (long long)q.t_end - kBuTile);
     const long long top = min((long long)q.t_end, base + kBuTile);
-    for (long long i = threadIdx.x; i < top - base; i += kNT)
-        S.tile[i] = make_float2(__ldg(q.x + base + i), __ldg(q.y + base + i));
+    stage_pair(S.tile, q.x + base, q.y + base, (int)(top - base), threadIdx.x, kNT);
     __syncthreads();
     if (threadIdx.x == 0) {
         S.tile_lo = base;

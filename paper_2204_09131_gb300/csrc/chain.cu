@@ -270,9 +270,11 @@ cudaError_t launch_chain(const ChainArgs &a, int n_chains, int max_cap, cudaStre
     ChainFn fn = chain_fn(a.k);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = chain_smem(max_cap);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is a property of the function, shared by every lane: always the largest ring's
+    // (a smaller value set by one lane would fail another lane's launch of a larger ring).
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chain_smem(kChainMaxCap));
     if (e != cudaSuccess) return e;
-    (void)cudaGetLastError();   // (an error left by an earlier call is not this launch's)
     fn<<<n_chains, kChainThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

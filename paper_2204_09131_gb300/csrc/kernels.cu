@@ -222,7 +222,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     {
         const int lane = threadIdx.x & 31;
         const int n_chunks = (m + 31) >> 5;
-        unsigned long long visits = 0;   // this warp's point x candidate visits
+        unsigned visits = 0;   // this warp's point x candidate visits (< 2^32 per window)
         for (;;) {
             int chunk = 0;
             if (lane == 0) chunk = atomicAdd(ctr, 1);
@@ -303,7 +303,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 }
             }
             // candidates visited: [L + 1, R), for the chunk's valid points
-            visits += (unsigned long long)(R - L - 1) * (unsigned long long)min(32, m - c0);
+            visits += (unsigned)(R - L - 1) * (unsigned)min(32, m - c0);
             if (valid) {
                 float dxm = 0.0f, dym = 0.0f;
                 int cc = 0;
@@ -323,7 +323,7 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                 pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
             }
         }
-        if (work && lane == 0) atomicAdd(work, visits);
+        if (work && lane == 0) atomicAdd(work, (unsigned long long)visits);
     }
     __syncthreads();
     // Phase B: the marginal counts by binary search, and the duplicate counts left open.
@@ -425,8 +425,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
         it.m = 0;
         if (has) it = a.items[first + slot];
         float2 *s = tile + (per_job == 1 ? 0 : slot * (kBlockPts * wpw));
-        if (has)
-            for (int i = sub * 32 + lane; i < it.m; i += wpw * 32) s[i] = make_float2(it.x[i], it.y[i]);
+        if (has) stage_pair(s, it.x, it.y, it.m, sub * 32 + lane, wpw * 32);
         if (lane == 0 && sub == 0) {
             acc_psi[slot] = 0;
             acc_log[slot] = 0;
@@ -542,7 +541,7 @@ __global__ void __launch_bounds__(NT) ksg_plain_kernel(WorkItem it, int k, const
     __shared__ long long sp[W], sl[W];
     __shared__ bool is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < it.m; i += NT) tile[i] = make_float2(it.x[i], it.y[i]);
+    stage_pair(tile, it.x, it.y, it.m, threadIdx.x, NT);
     __syncthreads();
     long long lp = 0, ll = 0;
     const int b = blockIdx.x * W + warp;
@@ -718,8 +717,8 @@ cudaError_t launch_plain(const WorkItem &it, int k, const long long *psi_fx,
     PlainFn fn = plain_fn(k);
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = (size_t)it.m * 8;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) {   // the largest window's limit, the same for every caller
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxM * 8);
         if (e != cudaSuccess) return e;
     }
     const int per_cta = (kPlainNT / 32) * kBlockPts;

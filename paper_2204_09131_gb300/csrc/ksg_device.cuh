@@ -226,6 +226,30 @@ __device__ __forceinline__ void ksg_block(Src s, int m, int base,
 }
 
 
+// Stage a window's m values of x and y into s as (x, y) pairs, by the threads t = tid,
+// tid + nt, ...: 16-byte loads of four consecutive values where x and y are equally aligned
+// (series buffers are, and the window's start is common to both), scalar loads for the
+// unaligned head and the tail.
+__device__ __forceinline__ void stage_pair(float2 *__restrict__ s, const float *__restrict__ x,
+                                           const float *__restrict__ y, int m, int tid, int nt) {
+    const uintptr_t ax = reinterpret_cast<uintptr_t>(x), ay = reinterpret_cast<uintptr_t>(y);
+    int head = m;
+    if (((ax ^ ay) & 15) == 0) head = min(m, (int)(((16 - (ax & 15)) & 15) >> 2));
+    for (int i = tid; i < head; i += nt) s[i] = make_float2(__ldg(x + i), __ldg(y + i));
+    const int nb = (m - head) >> 2;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x + head);
+    const float4 *y4 = reinterpret_cast<const float4 *>(y + head);
+    for (int i = tid; i < nb; i += nt) {
+        const float4 a = __ldg(x4 + i), b = __ldg(y4 + i);
+        float2 *d = s + head + 4 * i;
+        d[0] = make_float2(a.x, b.x);
+        d[1] = make_float2(a.y, b.y);
+        d[2] = make_float2(a.z, b.z);
+        d[3] = make_float2(a.w, b.w);
+    }
+    for (int i = head + 4 * nb + tid; i < m; i += nt) s[i] = make_float2(__ldg(x + i), __ldg(y + i));
+}
+
 // The window read in place from the resident series (broadcast loads through L1).
 struct PairSrc {
     const float *x;

@@ -129,16 +129,25 @@ uint32_t sort_mask(const isycos_ctx *ctx, int k) {
 // Build the persistent launch's bucket table for items already sorted by slot.
 static void build_table(BucketTable &T, const int32_t *count, int nt) { fill_bucket_table(&T, count, nt); }
 
+// The batched kernels' dynamic shared-memory limit is a property of the function, shared by
+// every thread and context of the process: it is set once to the device's maximum (less room
+// for the kernels' static shared memory), the same value every caller sets, and never
+// lowered, so that a launch on one lane cannot find the limit lowered by another.
 static isycos_status ensure_smem(isycos_ctx *ctx, int k, int nt, size_t smem) {
     std::lock_guard<std::mutex> g(ctx->launch_mu);
     int idx = nt == 1024 ? 1 : 0;
     if (smem <= ctx->smem_set[idx]) return ISYCOS_OK;
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
+    const size_t limit = (size_t)optin - 1024;
+    if (smem > limit) return fail(ctx, ISYCOS_E_INVAL, "a launch needs %zu bytes of shared memory", smem);
     for (int kk = 1; kk <= kMaxK; ++kk) {
-        cudaError_t e = set_batched_smem(kk, nt, smem);
+        e = set_batched_smem(kk, nt, limit);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     }
     (void)k;
-    ctx->smem_set[idx] = smem;
+    ctx->smem_set[idx] = limit;
     return ISYCOS_OK;
 }
 
@@ -582,26 +591,6 @@ const char *isycos_last_error(const isycos_ctx *ctx) {
     return ctx->err.c_str();
 }
 
-// Index of the first value of d[0..n) that is not finite (exponent bits all ones: an
-// infinity or a NaN), or -1.  Blocks are tested without a branch per value, so that the
-// scan vectorises; only a block that holds a bad value is searched again for its index.
-static int64_t first_nonfinite(const float *d, int64_t n) {
-    constexpr int64_t kBlock = 4096;
-    for (int64_t s = 0; s < n; s += kBlock) {
-        const int64_t e = std::min(n, s + kBlock);
-        uint32_t bad = 0;
-        for (int64_t i = s; i < e; ++i) {
-            uint32_t u;
-            memcpy(&u, d + i, 4);
-            bad |= (u & 0x7f800000u) == 0x7f800000u;
-        }
-        if (bad)
-            for (int64_t i = s; i < e; ++i)
-                if (!isfinite(d[i])) return i;
-    }
-    return -1;
-}
-
 // Device memory for a series of `bytes`: a buffer kept from a dropped series when one of
 // between `bytes` and twice that is free, else a new allocation (buffers kept from dropped
 // series are freed first when the budget or the device runs short).  Caller holds engine_mu.
@@ -650,12 +639,6 @@ static isycos_status put_series_list(isycos_ctx *ctx, int32_t count, const float
         if (!data[s] || n[s] < 1) return fail(ctx, ISYCOS_E_INVAL, "put_series: bad arguments (series %d)", s);
     std::lock_guard<std::mutex> g(ctx->engine_mu);
     cudaSetDevice(ctx->device);
-    if (!on_device)
-        for (int32_t s = 0; s < count; ++s) {
-            const int64_t i = first_nonfinite(data[s], n[s]);
-            if (i >= 0)
-                return fail(ctx, ISYCOS_E_INVAL, "put_series: value %lld of series %d is not finite", (long long)i, s);
-        }
     size_t free_slots = 0;
     for (float *p : ctx->series_ptr) free_slots += p ? 0 : 1;
     if (ctx->series_ptr.size() - free_slots + (size_t)count > (size_t)kMaxSeries)
@@ -675,8 +658,10 @@ static isycos_status put_series_list(isycos_ctx *ctx, int32_t count, const float
     for (int32_t s = 0; s < count && e == cudaSuccess; ++s)
         e = cudaMemcpyAsync(dev[s], data[s], sizeof(float) * (size_t)n[s],
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+    // every value is checked on the device once it is there (host input included: a scan on
+    // the device is faster than one on the host, and there is one synchronisation either way)
     int32_t bad = 0;
-    if (e == cudaSuccess && on_device) {
+    if (e == cudaSuccess) {
         if ((rc = dev_reserve(ctx, ctx->d_status, 256))) {
             cudaStreamSynchronize(ctx->stream);
             undo(count);
