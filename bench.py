@@ -873,8 +873,10 @@ def main():
                        "searches": "SYCOS_TD and SYCOS_BU queries of every pair, concurrently",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "autotune": {"sorted_buckets": tune["sorted_buckets"],
+                                    "sort_min": tune["sort_min"], "nt_switch": tune["nt_switch"],
                                     "window_size": tune["window_size"],
-                                    "brute_ms": tune["brute_ms"], "sorted_ms": tune["sorted_ms"]}},
+                                    "brute_ms": tune["brute_ms"], "sorted_ms": tune["sorted_ms"],
+                                    "crossover": tune["crossover"], "nt_ms": tune["nt_ms"]}},
             "pairs_per_s": round(pairs_per_s, 1),
             "pairs_note": "brute-force-equivalent ordered pairs m(m-1) per evaluated window",
             "windows_per_step": int(windows_all / args.steps),

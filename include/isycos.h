@@ -337,13 +337,21 @@ isycos_status isycos_reset_stats(isycos_ctx *ctx);
 isycos_status isycos_tables(isycos_ctx *ctx, int32_t n_max, int64_t *psi_fx, int64_t *log_fx);
 
 /* Autotuner.  The paper has no counterpart: its kNN search is a CPU index (Sec. 7.1).  For
- * k neighbours, times the brute-force and the sorted-strip MI paths on a seeded probe pair
- * (x ~ N(0,1), y = 0.6 x + 0.8 N(0,1), 65,536 points, uploaded and dropped by the call)
- * with one launch of n_windows windows (fewer for the two largest buckets) of the middle size
- * of each bucket the sorted path can take (windows of 257..16384 points), and keeps the faster
- * path per bucket for this context
- * and k (used while ISYCOS_OPT_KERNEL is 0, the default).  Results are identical on both
- * paths; only speed changes.  Statistics are left as they were.  out may be NULL.
+ * k neighbours, times launches on a seeded probe pair (x ~ N(0,1), y = 0.6 x + 0.8 N(0,1),
+ * 65,536 points, uploaded and dropped by the call) and keeps, for this context and k (used
+ * while ISYCOS_OPT_KERNEL is 0, the default):
+ *  - the faster of the brute-force and sorted-strip MI paths per size bucket the sorted path
+ *    can take (257..16384 points), each timed on n_windows windows of the bucket's middle
+ *    size (fewer for the two largest buckets);
+ *  - the crossover inside the smallest sorted bucket: windows below sort_min keep the
+ *    brute-force path (probed at 1/8, 2/8 and 3/8 into the bucket);
+ *  - nt_switch: launches whose largest sorted window exceeds it run 1024-thread CTAs, others
+ *    256-thread CTAs (512 or 1024, timed on windows of 768 points when their bucket is
+ *    sorted).
+ * Results are identical on every choice; only speed changes.  Statistics are left as they
+ * were.  When the environment names a file in ISYCOS_TUNING_FILE, the choice is stored there
+ * under the GPU's name and k (one line of JSON per entry), and isycos_create loads the
+ * entries of its GPU from it.  out may be NULL.
  * Errors: E_INVAL (k), E_NOMEM (budget), E_CUDA. */
 typedef struct {
     int32_t k;
@@ -354,8 +362,21 @@ typedef struct {
                                   buckets of 4097..8192 and 8193..16384 points)             */
     double brute_ms[15];       /* best of three launch times, brute-force path               */
     double sorted_ms[15];      /* best of three launch times, sorted-strip path              */
-} isycos_tuning;   /* 312 bytes */
+    int32_t sort_min;          /* smallest window size that takes the sorted path           */
+    int32_t nt_switch;         /* largest sorted window of a 256-thread launch               */
+    int32_t cross_size[3];     /* crossover probe sizes (0: not probed)                      */
+    int32_t pad;
+    double cross_brute_ms[3];  /* their launch times, brute force and sorted                 */
+    double cross_sorted_ms[3];
+    double nt_ms[2];           /* 768-point sorted windows in 256- and 1024-thread CTAs      */
+} isycos_tuning;   /* 400 bytes */
 isycos_status isycos_autotune(isycos_ctx *ctx, int32_t k, isycos_tuning *out);
+
+/* The tuning a context uses for k (from isycos_autotune or the tuning file): sorted buckets
+ * (bits as in isycos_tuning), sort_min and nt_switch.  E_NOTFOUND when k is not tuned (the
+ * defaults apply: buckets of 1025..16384 points sorted, sort_min 0, nt_switch 1024). */
+isycos_status isycos_get_tuning(isycos_ctx *ctx, int32_t k, uint32_t *sorted_buckets,
+                                int32_t *sort_min, int32_t *nt_switch);
 
 /* Options (isycos_set_option).  Values are documented per option. */
 #define ISYCOS_OPT_KERNEL 1        /* 0 auto (default: the buckets isycos_autotune chose, else

@@ -69,7 +69,11 @@ class isycos_params(ctypes.Structure):
 class isycos_tuning(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("sorted_buckets", ctypes.c_uint32),
                 ("window_size", ctypes.c_int32 * 15), ("n_windows", ctypes.c_int32),
-                ("brute_ms", ctypes.c_double * 15), ("sorted_ms", ctypes.c_double * 15)]
+                ("brute_ms", ctypes.c_double * 15), ("sorted_ms", ctypes.c_double * 15),
+                ("sort_min", ctypes.c_int32), ("nt_switch", ctypes.c_int32),
+                ("cross_size", ctypes.c_int32 * 3), ("pad", ctypes.c_int32),
+                ("cross_brute_ms", ctypes.c_double * 3), ("cross_sorted_ms", ctypes.c_double * 3),
+                ("nt_ms", ctypes.c_double * 2)]
 
 
 class isycos_query(ctypes.Structure):
@@ -144,6 +148,7 @@ SIGNATURES = {
     "isycos_tables": (_I32, [_VP, _I32, _VP, _VP]),
     "isycos_set_option": (_I32, [_VP, _I32, _I64]),
     "isycos_autotune": (_I32, [_VP, _I32, _VP]),
+    "isycos_get_tuning": (_I32, [_VP, _I32, _VP, _VP, _VP]),
     "isycos_mi_windows_noalloc": (_I32, [_VP, _VP, _I64, _VP, _VP, _I64, _I32, _I32, _VP, _VP]),
 }
 
@@ -453,11 +458,27 @@ def isycos_autotune(ctx, k: int = 4) -> dict:
     t = isycos_tuning()
     _check(ctx, lib().isycos_autotune(ctx, k, ctypes.byref(t)))
     buckets = [b for b in range(15) if t.window_size[b]]
+    cross = [i for i in range(3) if t.cross_size[i]]
     return {"k": t.k, "n_windows": t.n_windows,
             "sorted_buckets": [b for b in range(15) if (t.sorted_buckets >> b) & 1],
             "window_size": {b: t.window_size[b] for b in buckets},
             "brute_ms": {b: round(t.brute_ms[b], 4) for b in buckets},
-            "sorted_ms": {b: round(t.sorted_ms[b], 4) for b in buckets}}
+            "sorted_ms": {b: round(t.sorted_ms[b], 4) for b in buckets},
+            "sort_min": t.sort_min, "nt_switch": t.nt_switch,
+            "crossover": {t.cross_size[i]: {"brute_ms": round(t.cross_brute_ms[i], 4),
+                                            "sorted_ms": round(t.cross_sorted_ms[i], 4)} for i in cross},
+            "nt_ms": {"256": round(t.nt_ms[0], 4), "1024": round(t.nt_ms[1], 4)}}
+
+
+def isycos_get_tuning(ctx, k: int = 4):
+    """The tuning the context uses for k, or None when k is not tuned."""
+    sb, smin, nts = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_int32()
+    st = lib().isycos_get_tuning(ctx, k, ctypes.byref(sb), ctypes.byref(smin), ctypes.byref(nts))
+    if st == E_NOTFOUND:
+        return None
+    _check(ctx, st)
+    return {"sorted_buckets": [b for b in range(15) if (sb.value >> b) & 1], "sort_min": smin.value,
+            "nt_switch": nts.value}
 
 
 class Context:

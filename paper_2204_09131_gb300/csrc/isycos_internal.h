@@ -63,7 +63,7 @@ struct BatchArgs {
     uint32_t sort_mask;          // bit b set: windows of bucket b (2^(b-1) < m <= 2^b) that
                                  // run one per CTA take the sorted path
     int32_t est;                 // 0: Kraskov's second estimator (Eq. KSGmi), 1: the first
-    int32_t pad;
+    int32_t sort_min;            // windows below this size keep the brute-force path
     double inv_k;                // 1 / k correctly rounded (estimator 0), or 0 (estimator 1)
     unsigned char *gscratch;     // sorted-path scratch of windows above kSortMax points: one
     int64_t gscratch_stride;     // slice of gscratch_stride bytes per CTA (nullptr: none)
@@ -192,8 +192,9 @@ __host__ __device__ inline long long sort_cx_steps(int m) {
 // Whether a window of m points in a launch of nt-thread CTAs takes the sorted path (the
 // batched kernel's rule: windows of more than 64 points that run one per CTA, in a bucket of
 // sort_mask, with their scratch in shared memory or in the launch's global scratch).
-__host__ __device__ inline bool takes_sorted_path(int m, int nt, uint32_t sort_mask, bool gscratch) {
-    if (m <= 64) return false;
+__host__ __device__ inline bool takes_sorted_path(int m, int nt, uint32_t sort_mask, bool gscratch,
+                                                  int sort_min = 0) {
+    if (m <= 64 || m < sort_min) return false;
     const int q = kBuckets - 1 - size_bucket(m);
     const bool one_per_cta = nt / 32 / warps_per_item(q, nt) == 1;
     return one_per_cta && ((sort_mask >> size_bucket(m)) & 1u) && (m <= kSortMax || gscratch);
@@ -210,10 +211,11 @@ inline size_t batched_smem(int max_m, int nt, int max_sorted = 0) {
 
 // Threads per CTA chosen for a batch whose largest window has max_m points and whose
 // largest sorted-path window has max_sorted points (the sorted path runs one window per CTA:
-// above 1024 points it takes 1024 threads, which hide its dependent loads).  max_sorted
-// counts only windows whose scratch is in shared memory (at most kSortMax points).
-inline int batched_threads(int max_m, int max_sorted = 0) {
-    return (max_m > 8192 || max_sorted > 1024) ? 1024 : 256;
+// above nt_switch points, 1024 by default or as isycos_autotune chose, it takes 1024 threads,
+// which hide its dependent loads).  max_sorted counts only windows whose scratch is in
+// shared memory (at most kSortMax points).
+inline int batched_threads(int max_m, int max_sorted = 0, int nt_switch = 1024) {
+    return (max_m > 8192 || max_sorted > nt_switch) ? 1024 : 256;
 }
 
 }  // namespace isy

@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 4 : 1) ksg_batched_kernel(Batc
                 co = a.c + it.pts;
             }
             const bool sorted = per_job == 1 && ((a.sort_mask >> (32 - __clz(it.m - 1))) & 1u) &&
-                                (it.m <= kSortMax || a.gscratch != nullptr);
+                                it.m >= a.sort_min && (it.m <= kSortMax || a.gscratch != nullptr);
             if (sorted) {
                 unsigned char *scr = it.m <= kSortMax
                                          ? reinterpret_cast<unsigned char *>(tile) + sorted_off(it.m)

@@ -215,7 +215,7 @@ extern "C" isycos_status isycos_mi_windows_noalloc(const float *d_x, const float
     a.nt = nt;
     a.sort_mask = 0;          // brute-force path only
     a.est = 0;                // Kraskov's second estimator (Eq. KSGmi)
-    a.pad = 0;
+    a.sort_min = 0;
     a.inv_k = 1.0 / (double)k;
     a.gscratch = nullptr;
     a.gscratch_stride = 0;

@@ -126,6 +126,16 @@ uint32_t sort_mask(const isycos_ctx *ctx, int k) {
     return kDefaultSortBuckets;
 }
 
+int sort_min_size(const isycos_ctx *ctx, int k) {
+    if (ctx->opt_kernel != 0 || k < 1 || k > kMaxK || !ctx->tuned[k]) return 0;
+    return ctx->tuned_sort_min[k];
+}
+
+int nt_switch(const isycos_ctx *ctx, int k) {
+    if (ctx->opt_kernel != 0 || k < 1 || k > kMaxK || !ctx->tuned[k] || ctx->tuned_nt_switch[k] <= 0) return 1024;
+    return ctx->tuned_nt_switch[k];
+}
+
 // Build the persistent launch's bucket table for items already sorted by slot.
 static void build_table(BucketTable &T, const int32_t *count, int nt) { fill_bucket_table(&T, count, nt); }
 
@@ -185,6 +195,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     if (n > INT32_MAX / 2) return fail(ctx, ISYCOS_E_INVAL, "too many windows in one call");
     int max_m = 0, max_sorted = 0, max_sorted_glob = 0;
     const uint32_t smask = sort_mask(ctx, k);
+    const int smin = sort_min_size(ctx, k);
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
     std::vector<int32_t> &slot = L.h_slot;
@@ -195,7 +206,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
             return fail(ctx, ISYCOS_E_INVAL, "window %lld ([%lld, +%d] of series %d, %d) is outside its series",
                         (long long)i, (long long)w[i].start, w[i].m, w[i].xs, w[i].ys);
         max_m = std::max(max_m, w[i].m);
-        if ((smask >> size_bucket(w[i].m)) & 1u) {
+        if (((smask >> size_bucket(w[i].m)) & 1u) && w[i].m >= smin) {
             if (w[i].m <= kSortMax) max_sorted = std::max(max_sorted, w[i].m);
             else max_sorted_glob = std::max(max_sorted_glob, w[i].m);
         }
@@ -204,7 +215,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
         count[slot[i]]++;
         total_pts += w[i].m;
     }
-    const int nt = batched_threads(max_m, std::max(max_sorted, max_sorted_glob));
+    const int nt = batched_threads(max_m, std::max(max_sorted, max_sorted_glob), nt_switch(ctx, k));
     const size_t smem = batched_smem(max_m, nt, max_sorted);
     isycos_status rc;
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
@@ -272,7 +283,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     a.nt = nt;
     a.sort_mask = smask;
     a.est = est;
-    a.pad = 0;
+    a.sort_min = smin;
     a.inv_k = est ? 0.0 : 1.0 / (double)k;
     a.gscratch = max_sorted_glob > 0 ? reinterpret_cast<unsigned char *>(L.d_gscratch.p) : nullptr;
     a.gscratch_stride = (int64_t)g_stride;
@@ -282,7 +293,7 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     int64_t work_bf = 0, work_sort = 0;
     for (int64_t i = 0; i < n; ++i) {
         const int m = w[i].m;
-        if (takes_sorted_path(m, nt, smask, a.gscratch != nullptr)) work_sort += sort_cx_steps(m);
+        if (takes_sorted_path(m, nt, smask, a.gscratch != nullptr, smin)) work_sort += sort_cx_steps(m);
         else work_bf += (int64_t)m * m;
     }
     e = cudaEventRecord(L.ev_start, st);
@@ -545,6 +556,7 @@ isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budge
     {
         unsigned hw = std::thread::hardware_concurrency();
         ctx->max_lanes = (int)std::max(1u, std::min(12u, hw * 3 / 4));
+        load_tunings(ctx);   // choices isycos_autotune stored for this GPU, if any
         Lane *L0 = nullptr;
         if (get_lane(ctx, 0, &L0) != ISYCOS_OK) {
             isycos_destroy(ctx);
@@ -803,7 +815,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     int max_sorted = 0;
     for (int b = 1; b < 31; ++b)
         if (((smask >> b) & 1u) && (1 << (b - 1)) < max_m) max_sorted = std::min(std::min(max_m, 1 << b), kSortMax);
-    const int nt = batched_threads(max_m, max_sorted);
+    const int nt = batched_threads(max_m, max_sorted, nt_switch(ctx, k));
     const size_t smem = batched_smem(max_m, nt, max_sorted);
     if ((rc = ensure_smem(ctx, k, nt, smem))) return rc;
     if ((rc = dev_reserve(ctx, ctx->d_dev_items, sizeof(WorkItem) * n_w))) return rc;
@@ -848,7 +860,7 @@ isycos_status isycos_mi_windows_device(isycos_ctx *ctx, const isycos_window *d_w
     a.nt = nt;
     a.sort_mask = smask;
     a.est = ctx->opt_estimator;
-    a.pad = 0;
+    a.sort_min = sort_min_size(ctx, k);
     a.inv_k = a.est ? 0.0 : 1.0 / (double)k;
     a.gscratch = nullptr;   // windows above kSortMax points take the brute-force path here
     a.gscratch_stride = 0;

@@ -131,6 +131,8 @@ struct isycos_ctx {
     cudaEvent_t ev_bu[2] = {nullptr, nullptr};
     // sorted-path buckets chosen by isycos_autotune, per k (0: not tuned, use the default)
     uint32_t tuned_sort_mask[ISYCOS_MAX_K + 1] = {0};
+    int tuned_sort_min[ISYCOS_MAX_K + 1] = {0};     // windows below it keep brute force
+    int tuned_nt_switch[ISYCOS_MAX_K + 1] = {0};    // 0: 1024 (see batched_threads)
     bool tuned[ISYCOS_MAX_K + 1] = {false};
     int serve_slots = 64;
     int serve_queue = 100000;
@@ -178,8 +180,15 @@ void add_stats(isycos_ctx *ctx, int64_t windows, int64_t pairs, int64_t launches
 
 cudaStream_t pick_stream(isycos_ctx *ctx, void *s);
 
-// Size buckets whose windows take the sorted (sub-quadratic) MI path for k neighbours.
+// Size buckets whose windows take the sorted (sub-quadratic) MI path for k neighbours, the
+// smallest window that takes it, and the largest sorted window of a 256-thread launch.
 uint32_t sort_mask(const isycos_ctx *ctx, int k);
+int sort_min_size(const isycos_ctx *ctx, int k);
+int nt_switch(const isycos_ctx *ctx, int k);
+// Tunings kept in the file named by ISYCOS_TUNING_FILE (autotune.cu): load this device's
+// entries into the context; store one.
+void load_tunings(isycos_ctx *ctx);
+void store_tuning(const isycos_ctx *ctx, int k);
 
 // A window sequence of one pair for the incremental kernel: result i goes to out[out_idx[i]]
 // (out_idx < 0: evaluated for its state only, result dropped).

@@ -47,7 +47,7 @@ def test_struct_sizes_match_the_header():
     assert ctypes.sizeof(api.isycos_result_window) == 32
     assert ctypes.sizeof(api.isycos_params) == 104
     assert ctypes.sizeof(api.isycos_stats) == 632
-    assert ctypes.sizeof(api.isycos_tuning) == 312
+    assert ctypes.sizeof(api.isycos_tuning) == 400
 
 
 def test_params_defaults_follow_the_paper(lib):

@@ -417,6 +417,12 @@ def test_autotune_changes_speed_not_results(ctx):
     assert all(v > 0 for v in tune["brute_ms"].values()) and all(v > 0 for v in tune["sorted_ms"].values())
     for b in (9, 10, 11, 12, 13, 14):
         assert (b in tune["sorted_buckets"]) == (tune["sorted_ms"][b] < tune["brute_ms"][b])
+    assert tune["nt_switch"] in (512, 1024)
+    if tune["sorted_buckets"]:
+        b0 = min(tune["sorted_buckets"])
+        if b0 <= 12:
+            assert (1 << (b0 - 1)) < tune["sort_min"] <= tune["window_size"][b0]
+    assert api.isycos_get_tuning(ctx, 4) == {k: tune[k] for k in ("sorted_buckets", "sort_min", "nt_switch")}
     after = api.isycos_mi_windows(ctx, w, 4)
     assert np.array_equal(before, after)
     api.isycos_drop_series(ctx, xs)
@@ -564,3 +570,22 @@ def test_put_series_many_and_reuse_of_dropped_memory(ctx):
         for sid in ids:
             api.isycos_drop_series(ctx, sid)
         del dev
+
+
+def test_tuning_file_is_written_and_loaded(tmp_path, monkeypatch):
+    """isycos_autotune stores its choice under the GPU's name and k in ISYCOS_TUNING_FILE; a
+    context created later loads it (and a line for another GPU is left alone)."""
+    api = _api()
+    path = tmp_path / "tuning.json"
+    path.write_text('{"gpu": "another GPU", "k": 4, "sorted_buckets": 512, "sort_min": 300, "nt_switch": 512}\n')
+    monkeypatch.setenv("ISYCOS_TUNING_FILE", str(path))
+    with api.Context(0) as c1:
+        assert api.isycos_get_tuning(c1, 3) is None
+        tune = api.isycos_autotune(c1, 3)
+        got = api.isycos_get_tuning(c1, 3)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2 and "another GPU" in lines[0] and '"k": 3' in lines[1]
+    with api.Context(0) as c2:
+        assert api.isycos_get_tuning(c2, 3) == got
+        assert api.isycos_get_tuning(c2, 4) is None
+    assert got["sort_min"] == tune["sort_min"] and got["nt_switch"] == tune["nt_switch"]
