@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -198,6 +199,10 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     const int smin = sort_min_size(ctx, k);
     int64_t pairs = 0, total_pts = 0;
     int32_t count[kBuckets] = {0};
+    // for the work counters: sum of m^2 per size bucket, and the windows below sort_min in its
+    // bucket (the only bucket the sorted path splits)
+    int64_t m2_by_size[kBuckets] = {0}, m2_below = 0, n_below = 0;
+    const int b_smin = smin > 1 ? size_bucket(smin) : -1;
     std::vector<int32_t> &slot = L.h_slot;
     slot.resize((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
@@ -214,6 +219,13 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
         slot[i] = bucket_slot(w[i].m);
         count[slot[i]]++;
         total_pts += w[i].m;
+        const int64_t m2 = (int64_t)w[i].m * w[i].m;
+        const int b = kBuckets - 1 - slot[i];
+        m2_by_size[b] += m2;
+        if (b == b_smin && w[i].m < smin) {
+            m2_below += m2;
+            ++n_below;
+        }
     }
     const int nt = batched_threads(max_m, std::max(max_sorted, max_sorted_glob), nt_switch(ctx, k));
     const size_t smem = batched_smem(max_m, nt, max_sorted);
@@ -290,11 +302,19 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     // work counters: device accumulators after the work counters of d_queue
     a.work = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(L.d_queue.p) + 64);
     a.work_out = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(L.h_table.dev) + work_off);
+    // per bucket: the path is the same for all its windows (but those below sort_min); a
+    // sorted window's sort work depends on its bucket's slot count only
     int64_t work_bf = 0, work_sort = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        const int m = w[i].m;
-        if (takes_sorted_path(m, nt, smask, a.gscratch != nullptr, smin)) work_sort += sort_cx_steps(m);
-        else work_bf += (int64_t)m * m;
+    for (int b = 0; b < kBuckets; ++b) {
+        const int64_t nb = count[kBuckets - 1 - b];
+        if (nb == 0) continue;
+        if (b >= 7 && takes_sorted_path(1 << b, nt, smask, a.gscratch != nullptr)) {
+            const int64_t below = b == b_smin ? n_below : 0;
+            work_sort += (nb - below) * sort_cx_steps(1 << b);
+            work_bf += b == b_smin ? m2_below : 0;
+        } else {
+            work_bf += m2_by_size[b];
+        }
     }
     e = cudaEventRecord(L.ev_start, st);
     if (e == cudaSuccess) e = launch_batched(a, grid, smem, st);
@@ -329,11 +349,33 @@ isycos_status engine_launch(isycos_ctx *ctx, Lane &L, const HostWindow *w, int64
     return ISYCOS_OK;
 }
 
+constexpr int kSpinUs = 200;
+
 isycos_status engine_collect(isycos_ctx *ctx, Lane &L, isycos_mi_out *out) {
     Lane::Open &o = L.open;
     if (!o.open) return ISYCOS_OK;
     o.open = false;
-    cudaError_t e = cudaStreamSynchronize(o.st);
+    // A search round's launch usually finishes within tens of microseconds, and a blocking
+    // synchronise adds the host thread's wake-up to every round: poll the launch's stop event
+    // for up to kSpinUs first (the results are in mapped host memory once it has passed),
+    // then block.  Per-point outputs are copied after the launch: those wait for the stream.
+    cudaError_t e = cudaSuccess;
+    bool done = false;
+    if (!o.nx) {
+        const auto t_spin = std::chrono::steady_clock::now();
+        for (;;) {
+            e = cudaEventQuery(L.ev_stop);
+            if (e != cudaErrorNotReady) {
+                done = e == cudaSuccess;
+                break;
+            }
+            if (std::chrono::steady_clock::now() - t_spin > std::chrono::microseconds(kSpinUs)) {
+                e = cudaSuccess;
+                break;
+            }
+        }
+    }
+    if (!done && e == cudaSuccess) e = cudaStreamSynchronize(o.st);
     float t0 = 0.0f, t1 = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ctx->ev_ref, L.ev_start);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev_ref, L.ev_stop);
