@@ -166,13 +166,15 @@ __host__ __device__ inline int size_bucket(int m) {   // smallest b with m <= 2^
 }
 
 // Sorted path layout in shared memory after the window's m float2 values: the sort keys
-// (8 bytes per slot, the slot count rounded up to a power of two), the x-ordered records
-// (16 bytes per point), per-point d_x, d_y and multiplicity (12 bytes), a work counter.
+// (8 bytes per slot, the slot count rounded up to a power of two; the y order once the x
+// order is in the records), the x-ordered records (16 bytes per point), per-point d_x, d_y
+// and multiplicity (12 bytes), four counters, one bit per point of the y order (a word per
+// 32 points).
 __host__ __device__ inline size_t sorted_off(int m) { return ((size_t)m * 8 + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t sorted_scratch(int m) {   // the part after the window
     int n = 1;
     while (n < m) n <<= 1;
-    return (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16;
+    return (size_t)8 * n + (size_t)16 * m + (size_t)12 * m + 16 + (size_t)4 * ((m + 31) / 32);
 }
 __host__ __device__ inline size_t sorted_smem(int m) { return sorted_off(m) + sorted_scratch(m); }
 

@@ -40,11 +40,13 @@ namespace {
 
 // ---------------------------------------------------------------------------------------
 // Sub-quadratic path for one large window (all threads of the CTA), the sorted-strip form of
-// the box-assisted search of Sec. 7.1: the window's points are sorted by x; each point's
-// neighbours are searched outward along the sorted order, nearest x first, until the x
-// distance on both sides exceeds the current k+1-th distance (no farther point can enter,
-// since d >= |dx|); the marginal counts are ranges of the x- and y-sorted values found by
-// binary search, because fl(|x_i - x_j|) is monotone along the sorted order.  Candidates
+// the box-assisted search of Sec. 7.1: the window's points are sorted by x and by y; each
+// point's neighbours are searched outward along one of the two orders, nearest first in that
+// coordinate, until its distance on both sides exceeds the current k+1-th distance (no
+// farther point can enter, since d >= |dx| and d >= |dy|); a point takes the y order when
+// its y strip is much shorter than its x strip.  The marginal counts are ranges of the x-
+// and y-sorted values found by binary search, because fl(|x_i - x_j|) is monotone along the
+// sorted order.  Candidates
 // arrive out of time order, so the neighbour list compares (d, j) lexicographically.  Every
 // comparison is the same binary32 operation as in the brute-force path: results are equal.
 // ---------------------------------------------------------------------------------------
@@ -177,7 +179,154 @@ __host__ __device__ inline int pow2_ceil(int m) {
     return n;
 }
 
-// work (optional): [0] += phase A point x candidate visits, [1] += phase B search and
+// Value of a y key (fkey of the value in the upper 32 bits); zero decodes to +0, which
+// subtracts and compares like -0.
+__device__ __forceinline__ float key_val(unsigned long long k) {
+    const uint32_t u = (uint32_t)(k >> 32);
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// A candidate of the outward scans as (x, y, j): position u of the x order (a record) or of
+// the y order (a key, whose index selects the window's value).
+template <bool Y>
+__device__ __forceinline__ float4 cand(const float4 *rec, const unsigned long long *keys,
+                                       const float2 *s, int u) {
+    if constexpr (Y) {
+        const int j = (int)(keys[u] & 0xffffffffu);
+        const float2 v = s[j];
+        return make_float4(v.x, v.y, __int_as_float(j), 0.0f);
+    } else {
+        return rec[u];
+    }
+}
+
+// The coordinate a scan in that order is sorted by, at position u.
+template <bool Y>
+__device__ __forceinline__ float ord_val(const float4 *rec, const unsigned long long *keys, int u) {
+    if constexpr (Y) return key_val(keys[u]);
+    else return rec[u].x;
+}
+
+// Candidates u, u + dir, u + 2 dir, u + 3 dir into the list of the point (xi, yi): loads and
+// distances first, then the insertions (the list is the same in any visiting order).
+template <int K1, bool Y>
+__device__ __forceinline__ void visit4(const float4 *rec, const unsigned long long *keys,
+                                       const float2 *s, float xi, float yi, float (&bd)[K1],
+                                       int (&bj)[K1], int u, int dir) {
+    float4 c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = cand<Y>(rec, keys, s, u + q * dir);
+    float d[4];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        d[q] = fmaxf(fabsf(xi - c[q].x), fabsf(yi - c[q].y));
+        any |= d[q] <= bd[K1 - 1];
+    }
+    if (any) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int jj = __float_as_int(c[q].z);
+            if (d[q] < bd[K1 - 1] || (d[q] == bd[K1 - 1] && jj < bj[K1 - 1]))
+                insert_lex<K1>(bd, bj, d[q], jj);
+        }
+    }
+}
+
+template <int K1, bool Y>
+__device__ __forceinline__ void visit1(const float4 *rec, const unsigned long long *keys,
+                                       const float2 *s, float xi, float yi, float (&bd)[K1],
+                                       int (&bj)[K1], int u) {
+    const float4 c = cand<Y>(rec, keys, s, u);
+    const float d = fmaxf(fabsf(xi - c.x), fabsf(yi - c.y));
+    const int jj = __float_as_int(c.z);
+    if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
+}
+
+// Positions [a0, a1) of the order, every lane of the warp.
+template <int K1, bool Y>
+__device__ __forceinline__ void visit_range(const float4 *rec, const unsigned long long *keys,
+                                            const float2 *s, float xi, float yi, float (&bd)[K1],
+                                            int (&bj)[K1], int a0, int a1) {
+    int u = a0;
+    for (; u + 4 <= a1; u += 4) visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, u, 1);
+    for (; u < a1; ++u) visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, u);
+}
+
+// Extend the scanned positions (L, R) outward, 8 at a time on each side, while the next
+// position on that side is within the bound of some active lane along the order's coordinate
+// ci.  The bound is the lane's current k+1-th distance, or bnd if smaller (an upper bound of
+// the final one): a point farther than it along the coordinate cannot enter the list
+// (d >= that coordinate's distance), and along the order that distance only grows (binary32
+// subtraction is monotone) while the bounds only shrink.  Control is warp-uniform: every
+// lane visits the same candidates (broadcast shared loads).
+template <int K1, bool Y>
+__device__ __forceinline__ void extend(const float4 *rec, const unsigned long long *keys,
+                                       const float2 *s, float xi, float yi, bool act, float bnd,
+                                       float (&bd)[K1], int (&bj)[K1], int &L, int &R, int m) {
+    const float ci = Y ? yi : xi;
+    for (;;) {
+        const bool need_l = L >= 0 &&
+            __any_sync(kFull, act && fabsf(ci - ord_val<Y>(rec, keys, L)) <= fminf(bd[K1 - 1], bnd));
+        const bool need_r = R < m &&
+            __any_sync(kFull, act && fabsf(ci - ord_val<Y>(rec, keys, R)) <= fminf(bd[K1 - 1], bnd));
+        if (!need_l && !need_r) break;
+        if (need_l) {
+            if (L >= 7) {
+                visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, L, -1);
+                visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, L - 4, -1);
+                L -= 8;
+            } else {
+                for (; L >= 0; --L) visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, L);
+            }
+        }
+        if (need_r) {
+            if (R + 8 <= m) {
+                visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, R, 1);
+                visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, R + 4, 1);
+                R += 8;
+            } else {
+                for (; R < m; ++R) visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, R);
+            }
+        }
+    }
+}
+
+// The strip [lo, hi] of positions around t (value c at t) whose values v(u) satisfy
+// |c - v(u)| <= e, by binary search (the predicate holds on a range around t, since the
+// values ascend); an empty strip (e < 0) leaves [t, t].  steps counts the search steps.
+template <typename V>
+__device__ __forceinline__ void strip_around(V v, float c, float e, int t, int m, int &lo, int &hi,
+                                             int &steps) {
+    int l0 = 0, l1 = t;
+    while (l0 < l1) {
+        ++steps;
+        const int mid = (l0 + l1) >> 1;
+        if (fabsf(c - v(mid)) <= e) l1 = mid;
+        else l0 = mid + 1;
+    }
+    int r0 = t, r1 = m - 1;
+    while (r0 < r1) {
+        ++steps;
+        const int mid = (r0 + r1 + 1) >> 1;
+        if (fabsf(c - v(mid)) <= e) r0 = mid;
+        else r1 = mid - 1;
+    }
+    lo = l0;
+    hi = r0;
+}
+
+// A point searches along the y order instead of the x order when the y values around it are
+// this many times sparser than the x values around it (mean gaps over 64 positions of each
+// order), so that the same bound holds that many times fewer points in its y strip.
+constexpr float kYSparser = 2.0f;
+// Windows of at most this many points keep every search on the x order.
+constexpr int kYOrderMin = 1024;
+// The seed of a chunk's scans: the positions [c0 - kSeedBefore, c0 + kSeedAfter) of the order
+// around a chunk of 32 positions from c0.
+constexpr int kSeedBefore = 16, kSeedAfter = 48;
+
+// work (optional): [0] += phase A point x candidate visits, [1] += search and
 // duplicate-scan steps.
 template <int K1, int NT>
 __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned char *scratch,
@@ -187,8 +336,20 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
                                   int32_t *c_out, int est, unsigned long long *work) {
     const float kInf = __int_as_float(0x7f800000);
     const int N = pow2_ceil(m);
+    const int n_chunks = (m + 31) >> 5;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(scratch);
     float4 *rec = reinterpret_cast<float4 *>(scratch + (size_t)8 * N);
+    float *pdx = reinterpret_cast<float *>(scratch + (size_t)8 * N + (size_t)16 * m);
+    float *pdy = pdx + m;
+    int *pcc = reinterpret_cast<int *>(pdy + m);
+    int *ctr = pcc + m;
+    unsigned *ymask = reinterpret_cast<unsigned *>(ctr + 4);
+
+    // The x order as records (x, y, j, y position), then the y order as keys (value, j) in the
+    // same slots (pcc holds each point's x position meanwhile); a window that keeps every
+    // search on the x order needs only the sorted y values there.
+    const bool two = m > kYOrderMin;
+    float *ysf = reinterpret_cast<float *>(keys);
     for (int i = threadIdx.x; i < N; i += NT)
         keys[i] = i < m ? (((unsigned long long)fkey(s[i].x) << 32) | (unsigned)i) : ~0ull;
     __syncthreads();
@@ -196,190 +357,180 @@ __device__ void ksg_window_sorted(const float2 *__restrict__ s, int m, unsigned 
     for (int t = threadIdx.x; t < m; t += NT) {
         const int j = (int)(keys[t] & 0xffffffffu);
         rec[t] = make_float4(s[j].x, s[j].y, __int_as_float(j), 0.0f);
+        pcc[j] = t;
     }
     __syncthreads();
-    float *ys = reinterpret_cast<float *>(keys);   // the keys are no longer needed
-    for (int i = threadIdx.x; i < N; i += NT) ys[i] = i < m ? s[i].y : kInf;
+    for (int i = threadIdx.x; i < n_chunks; i += NT) ymask[i] = 0u;
+    if (threadIdx.x < 4) ctr[threadIdx.x] = 0;
+    if (two) {
+        for (int i = threadIdx.x; i < N; i += NT)
+            keys[i] = i < m ? (((unsigned long long)fkey(s[i].y) << 32) | (unsigned)i) : ~0ull;
+        __syncthreads();
+        sort_keys<NT>(keys, N);
+        for (int p = threadIdx.x; p < m; p += NT)
+            rec[pcc[(int)(keys[p] & 0xffffffffu)]].w = __int_as_float(p);
+    } else {
+        for (int i = threadIdx.x; i < N; i += NT) ysf[i] = i < m ? s[i].y : kInf;
+        __syncthreads();
+        sort_keys<NT>(ysf, N);
+    }
     __syncthreads();
-    sort_keys<NT>(ys, N);
 
-    // Phase A: the neighbour lists, by outward scans.  A warp takes 32 consecutive points of
-    // the x order (a chunk, from a shared counter).  Every lane first scans the 64 points of
-    // the x order around the chunk, which gives its point a list of k + 1 and so a bound on
-    // its (k+1)-th distance.  The warp then extends the scanned range outward, 8 points at a
-    // time on each side, while the next point on that side is within some lane's bound in
-    // x: a point farther in x than a lane's bound cannot enter its list (d >= |dx|), and
-    // along the x order |x_i - x| only grows (binary32 rounding is monotone), while the
-    // bounds only shrink.  Every lane visits the same candidates (broadcast shared loads,
-    // warp-uniform control).  Per point it leaves d_x, d_y and the multiplicity (or -1 when
-    // the (k+1)-th distance is 0 and the duplicates must be counted in phase B).
-    float *pdx = reinterpret_cast<float *>(scratch + (size_t)8 * N + (size_t)16 * m);
-    float *pdy = pdx + m;
-    int *pcc = reinterpret_cast<int *>(pdy + m);
-    int *ctr = pcc + m;
-    if (threadIdx.x == 0) *ctr = 0;
-    __syncthreads();
-    {
-        const int lane = threadIdx.x & 31;
-        const int n_chunks = (m + 31) >> 5;
-        unsigned visits = 0;   // this warp's point x candidate visits (< 2^32 per window)
-        for (;;) {
-            int chunk = 0;
-            if (lane == 0) chunk = atomicAdd(ctr, 1);
-            chunk = __shfl_sync(kFull, chunk, 0);
-            if (chunk >= n_chunks) break;
-            const int c0 = chunk << 5;
-            const int t = c0 + lane;
-            const bool valid = t < m;
-            float xi = kInf, yi = kInf;
-            if (valid) {
-                const float4 me = rec[t];
-                xi = me.x;
-                yi = me.y;
-            }
-            float bd[K1];
-            int bj[K1];
+    // Phase A: the neighbour lists, by outward scans along one of the two orders (the list is
+    // the first k + 1 entries of (d, j) over the window, whatever the order of the visits).
+    // Per point it leaves, indexed by j, d_x, d_y and the multiplicity (or -1 when the
+    // (k+1)-th distance is 0 and the duplicates must be counted in phase B).
+    const int lane = threadIdx.x & 31;
+    int steps = 0;          // this thread's search and scan steps
+    unsigned visits = 0;    // this warp's point x candidate visits (< 2^32 per window)
+    auto finish = [&](float xi, float yi, int ji, const float (&bd)[K1], const int (&bj)[K1]) {
+        float dxm = 0.0f, dym = 0.0f;
+        int cc = 0;
 #pragma unroll
-            for (int r = 0; r < K1; ++r) {
-                bd[r] = kInf;
-                bj[r] = 0x7fffffff;
-            }
-            auto visit = [&](int u) {
-                const float4 c = rec[u];
-                const float d = fmaxf(fabsf(xi - c.x), fabsf(yi - c.y));
-                const int jj = __float_as_int(c.z);
-                if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
-            };
-            // four candidates u, u + dir, u + 2 dir, u + 3 dir: loads and distances first, then
-            // the insertions (the list is the same in any visiting order)
-            auto visit4 = [&](int u, int dir) {
-                float4 c[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) c[q] = rec[u + q * dir];
-                float d[4];
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    d[q] = fmaxf(fabsf(xi - c[q].x), fabsf(yi - c[q].y));
-                    any |= d[q] <= bd[K1 - 1];
-                }
-                if (any) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jj = __float_as_int(c[q].z);
-                        if (d[q] < bd[K1 - 1] || (d[q] == bd[K1 - 1] && jj < bj[K1 - 1]))
-                            insert_lex<K1>(bd, bj, d[q], jj);
-                    }
-                }
-            };
-            // the 64 points around the chunk (the point itself among them)
-            const int a0 = max(0, c0 - 16), a1 = min(m, c0 + 48);
-            int u = a0;
-            for (; u + 4 <= a1; u += 4) visit4(u, 1);
-            for (; u < a1; ++u) visit(u);
-            // outward, while some lane's strip reaches the next point
-            int L = a0 - 1, R = a1;
-            for (;;) {
-                const bool need_l = L >= 0 && __any_sync(kFull, valid && fabsf(xi - rec[L].x) <= bd[K1 - 1]);
-                const bool need_r = R < m && __any_sync(kFull, valid && fabsf(xi - rec[R].x) <= bd[K1 - 1]);
-                if (!need_l && !need_r) break;
-                if (need_l) {
-                    if (L >= 7) {
-                        visit4(L, -1);
-                        visit4(L - 4, -1);
-                        L -= 8;
-                    } else {
-                        for (; L >= 0; --L) visit(L);
-                    }
-                }
-                if (need_r) {
-                    if (R + 8 <= m) {
-                        visit4(R, 1);
-                        visit4(R + 4, 1);
-                        R += 8;
-                    } else {
-                        for (; R < m; ++R) visit(R);
-                    }
-                }
-            }
-            // candidates visited: [L + 1, R), for the chunk's valid points
-            visits += (unsigned)(R - L - 1) * (unsigned)min(32, m - c0);
-            if (valid) {
-                float dxm = 0.0f, dym = 0.0f;
-                int cc = 0;
-#pragma unroll
-                for (int r = 0; r < K1; ++r) {
-                    const float2 v = s[bj[r]];
-                    dxm = fmaxf(dxm, fabsf(xi - v.x));
-                    dym = fmaxf(dym, fabsf(yi - v.y));
-                    cc += bd[r] == 0.0f ? 1 : 0;
-                }
-                if (est) {   // Kraskov's first estimator: strict strips of half-width eps
-                    const float e = bd[K1 - 1];
-                    dxm = dym = e > 0.0f ? __int_as_float(__float_as_int(e) - 1) : -1.0f;
-                }
-                pdx[t] = dxm;
-                pdy[t] = dym;
-                pcc[t] = bd[K1 - 1] == 0.0f ? -1 : cc;
-            }
+        for (int r = 0; r < K1; ++r) {
+            const float2 v = s[bj[r]];
+            dxm = fmaxf(dxm, fabsf(xi - v.x));
+            dym = fmaxf(dym, fabsf(yi - v.y));
+            cc += bd[r] == 0.0f ? 1 : 0;
         }
-        if (work && lane == 0) atomicAdd(work, (unsigned long long)visits);
+        if (est) {   // Kraskov's first estimator: strict strips of half-width eps
+            const float e = bd[K1 - 1];
+            dxm = dym = e > 0.0f ? __int_as_float(__float_as_int(e) - 1) : -1.0f;
+        }
+        pdx[ji] = dxm;
+        pdy[ji] = dym;
+        pcc[ji] = bd[K1 - 1] == 0.0f ? -1 : cc;
+    };
+    // A1: a warp takes 32 consecutive points of the x order (a chunk, from a shared counter)
+    // and scans the seed positions of the x order around it, which gives every point a list
+    // of k + 1 and so a bound b on its (k+1)-th distance.  In a window of more than kYOrderMin
+    // points, a point whose strip reaches past the seed and whose y neighbourhood is kYSparser
+    // times sparser than its x neighbourhood leaves its search to A2 (a bit at its y position)
+    // with b; the other points of the chunk go on outward along the x order.
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(ctr, 1);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        if (chunk >= n_chunks) break;
+        const int c0 = chunk << 5;
+        const int t = c0 + lane;
+        const bool valid = t < m;
+        float xi = kInf, yi = kInf;
+        int ji = 0, py = 0;
+        if (valid) {
+            const float4 me = rec[t];
+            xi = me.x;
+            yi = me.y;
+            ji = __float_as_int(me.z);
+            py = __float_as_int(me.w);
+        }
+        // (a list at -inf takes no candidate: lanes without a point skip the insertions)
+        float bd[K1];
+        int bj[K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            bd[r] = valid ? kInf : -kInf;
+            bj[r] = 0x7fffffff;
+        }
+        const int a0 = max(0, c0 - kSeedBefore), a1 = min(m, c0 + kSeedAfter);
+        visit_range<K1, false>(rec, keys, s, xi, yi, bd, bj, a0, a1);
+        visits += (unsigned)(a1 - a0) * (unsigned)min(32, m - c0);
+        int L = a0 - 1, R = a1;
+        bool act = valid;
+        const bool more = valid && ((L >= 0 && fabsf(xi - rec[L].x) <= bd[K1 - 1]) ||
+                                    (R < m && fabsf(xi - rec[R].x) <= bd[K1 - 1]));
+        if (__any_sync(kFull, more)) {
+            if (more && two) {
+                // mean gaps: x over the seed positions, y over 64 positions around py
+                const int pl = max(0, py - 32), pr = min(m - 1, py + 32);
+                const float gx = (rec[a1 - 1].x - rec[a0].x) * (float)(pr - pl);
+                const float gy = (key_val(keys[pr]) - key_val(keys[pl])) * (float)(a1 - 1 - a0);
+                if (gy > kYSparser * gx) {
+                    act = false;
+                    pdx[ji] = bd[K1 - 1];
+                    atomicOr(ymask + (py >> 5), 1u << (py & 31));
+#pragma unroll
+                    for (int r = 0; r < K1; ++r) bd[r] = -kInf;
+                }
+            }
+            const int w0 = R - L - 1;
+            extend<K1, false>(rec, keys, s, xi, yi, act, kInf, bd, bj, L, R, m);
+            visits += (unsigned)(R - L - 1 - w0) * (unsigned)__popc(__ballot_sync(kFull, act));
+        }
+        if (act) finish(xi, yi, ji, bd, bj);
     }
+    __syncthreads();
+    // A2: a warp takes 32 consecutive positions of the y order whose bits are set and scans
+    // the seed positions around them, then outward along the y order, for those points alone
+    // (new lists; b bounds the strips from the start).
+    while (two) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(ctr + 1, 1);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        if (chunk >= n_chunks) break;
+        const unsigned mk = ymask[chunk];
+        if (mk == 0u) continue;
+        const int c0 = chunk << 5;
+        const bool act = (mk >> lane) & 1u;
+        float xi = kInf, yi = kInf, bnd = kInf;
+        int ji = 0;
+        if (act) {
+            ji = (int)(keys[c0 + lane] & 0xffffffffu);
+            const float2 v = s[ji];
+            xi = v.x;
+            yi = v.y;
+            bnd = pdx[ji];
+        }
+        float bd[K1];
+        int bj[K1];
+#pragma unroll
+        for (int r = 0; r < K1; ++r) {
+            bd[r] = act ? kInf : -kInf;
+            bj[r] = 0x7fffffff;
+        }
+        const int a0 = max(0, c0 - kSeedBefore), a1 = min(m, c0 + kSeedAfter);
+        visit_range<K1, true>(rec, keys, s, xi, yi, bd, bj, a0, a1);
+        int L = a0 - 1, R = a1;
+        extend<K1, true>(rec, keys, s, xi, yi, act, bnd, bd, bj, L, R, m);
+        visits += (unsigned)(R - L - 1) * (unsigned)__popc(mk);
+        if (act) finish(xi, yi, ji, bd, bj);
+    }
+    if (work && lane == 0) atomicAdd(work, (unsigned long long)visits);
     __syncthreads();
     // Phase B: the marginal counts by binary search, and the duplicate counts left open.
-    int steps = 0;   // this thread's search and scan steps
     for (int t = threadIdx.x; t < m; t += NT) {
         const float4 me = rec[t];
         const float xi = me.x, yi = me.y;
         const int ji = __float_as_int(me.z);
-        const float dxm = pdx[t], dym = pdy[t];
+        const float dxm = pdx[ji], dym = pdy[ji];
         // n_x: the x-sorted range around position t where fabsf(x_i - x) <= d_x
-        int l0 = 0, l1 = t;
-        while (l0 < l1) {
-            ++steps;
-            const int mid = (l0 + l1) >> 1;
-            if (fabsf(xi - rec[mid].x) <= dxm) l1 = mid;
-            else l0 = mid + 1;
-        }
-        int r0 = t, r1 = m - 1;
-        while (r0 < r1) {
-            ++steps;
-            const int mid = (r0 + r1 + 1) >> 1;
-            if (fabsf(xi - rec[mid].x) <= dxm) r0 = mid;
-            else r1 = mid - 1;
-        }
+        int l0, r0;
+        strip_around([&](int u) { return rec[u].x; }, xi, dxm, t, m, l0, r0, steps);
         const int cx = r0 - l0 + 1;
-        // n_y: the same on the y-sorted values, around the first value >= y_i
-        int p0 = 0, p1 = m;
-        while (p0 < p1) {
-            ++steps;
-            const int mid = (p0 + p1) >> 1;
-            if (ys[mid] < yi) p0 = mid + 1;
-            else p1 = mid;
-        }
-        const int piv = p0;
-        int q0 = 0, q1 = piv;
-        while (q0 < q1) {
-            ++steps;
-            const int mid = (q0 + q1) >> 1;
-            if (fabsf(yi - ys[mid]) <= dym) q1 = mid;
-            else q0 = mid + 1;
-        }
-        int w0 = piv, w1 = m - 1;
-        while (w0 < w1) {
-            ++steps;
-            const int mid = (w0 + w1 + 1) >> 1;
-            if (fabsf(yi - ys[mid]) <= dym) w0 = mid;
-            else w1 = mid - 1;
+        // n_y: the same on the y-sorted values, around the point's own y position (or the first
+        // value >= y_i)
+        int q0, w0;
+        if (two) {
+            strip_around([&](int u) { return key_val(keys[u]); }, yi, dym, __float_as_int(me.w), m, q0,
+                         w0, steps);
+        } else {
+            int p0 = 0, p1 = m;
+            while (p0 < p1) {
+                ++steps;
+                const int mid = (p0 + p1) >> 1;
+                if (ysf[mid] < yi) p0 = mid + 1;
+                else p1 = mid;
+            }
+            strip_around([&](int u) { return ysf[u]; }, yi, dym, p0, m, q0, w0, steps);
         }
         const int cy = w0 - q0 + 1;
-        int cc = pcc[t];
+        int cc = pcc[ji];
         if (cc < 0) {   // k+1-th distance 0: count the duplicates among the equal x values
             cc = 1;
             for (int u = t - 1; u >= 0 && rec[u].x == xi; --u, ++steps) cc += rec[u].y == yi ? 1 : 0;
             for (int u = t + 1; u < m && rec[u].x == xi; ++u, ++steps) cc += rec[u].y == yi ? 1 : 0;
         }
-        // (an empty strip, t < 0, leaves the search ranges at the point itself: count 1)
+        // (an empty strip, e < 0, leaves the search ranges at the point itself: count 1)
         const int nxv = cx - 1, nyv = cy - 1;
         acc_psi += __ldg(psi_fx + nxv + est) + __ldg(psi_fx + nyv + est);
         acc_log += __ldg(log_fx + cc);
