@@ -461,6 +461,45 @@ def test_ring_shaped_batch_all_paths_agree(ctx):
     api.isycos_drop_series(ctx, ys)
 
 
+def test_sorted_path_y_order_points(ctx):
+    """Above 1,024 points the sorted path sends a point whose y neighbourhood is sparse (far
+    from the others in y) to a second scan along the y order.  Heavy-tailed y values (a
+    ratio of normals), coarse ties in y among those outliers, ties in x, and heavy tails in
+    both coordinates make many points take it; per point the results equal the brute-force
+    path for k = 1, 4 and 8, and one window per case equals the oracle."""
+    api = _api()
+    n = 40000
+    a = synth.normal(synth.seed_for(206, 0), n)
+    b = synth.normal(synth.seed_for(206, 1), n)
+    c = synth.normal(synth.seed_for(206, 2), n)
+    heavy = (b / np.where(np.abs(c) < 1e-3, 1e-3, c)).astype(np.float32)   # Cauchy-like tails
+    x = a.astype(np.float32)
+    cases = [(x, heavy), (x, synth.quantize(heavy, 0.5)), (synth.quantize(x, 4.0), heavy),
+             ((a / np.where(np.abs(b) < 1e-3, 1e-3, b)).astype(np.float32), heavy)]
+    sizes = [1025, 1800, 2048, 3333, 4096, 4097, 7000, 16384]
+    starts = [100 + 2900 * i for i in range(len(sizes))]
+    try:
+        for ci, (xx, yy) in enumerate(cases):
+            xs, ys = api.isycos_put_series(ctx, xx), api.isycos_put_series(ctx, yy)
+            w = api.windows_array(xs, ys, starts, sizes)
+            for k in (1, 4, 8):
+                res = {}
+                for opt in (1, 2):
+                    api.isycos_set_option(ctx, api.OPT_KERNEL, opt)
+                    res[opt] = api.isycos_mi_windows_points(ctx, w, k)
+                for u, v in zip(res[1], res[2]):
+                    assert np.array_equal(u, v), (ci, k)
+            s0, m0 = starts[1], sizes[1]
+            r = O.ksg_window(xx[s0:s0 + m0], yy[s0:s0 + m0], 4, points=False)
+            api.isycos_set_option(ctx, api.OPT_KERNEL, 2)
+            got = api.isycos_mi_windows(ctx, api.windows_array(xs, ys, [s0], [m0]), 4)
+            assert got["s_psi"][0] == r["s_psi"] and got["s_log"][0] == r["s_log"], ci
+            api.isycos_drop_series(ctx, xs)
+            api.isycos_drop_series(ctx, ys)
+    finally:
+        api.isycos_set_option(ctx, api.OPT_KERNEL, 0)
+
+
 def test_sorted_path_repeats_bit_exact(ctx):
     """The sorted path's sorts and scans synchronise warps and CTAs in many small steps; a
     missing barrier shows up as run-to-run differences.  Repeat mixed batches (256- and
