@@ -432,7 +432,46 @@ def config1_full():
             "sweep_evals_per_s": round(len(wins) / t_sweep, 1), "searches": searches}
 
 
-def cpu_baseline(pairs, decided_by_size=None, steps=1, prefix=12000):
+def _oracle_search_job(job):
+    """The oracle's SYCOS_TD + SYCOS_BU on the first `prefix` points of pair p (config-2
+    shape); run in a spawned worker.  Returns the window scores it read."""
+    p, length, prefix = job
+    from oracle import oracle as O
+    from paper_2204_09131_gb300 import synth
+    x, y, _ = synth.planted_pair(2, p, length)
+    _, n1 = O.search_td(x[:prefix], y[:prefix], **PARAMS)
+    _, n2 = O.search_bu(x[:prefix], y[:prefix], **PARAMS)
+    return n1 + n2
+
+
+def oracle_multicore(n_pairs, length, prefix):
+    """The same oracle searches on `n_pairs` pairs at once, one single-threaded process per
+    core the host lets this process use (spawned workers, started before they are timed)."""
+    import multiprocessing as mp
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    cores = max(1, min(cores, n_pairs))
+    jobs = [(p, length, prefix) for p in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_job_ready, range(cores))   # workers up and imports done
+        t0 = time.perf_counter()
+        evals = sum(pool.map(_oracle_search_job, jobs, chunksize=1))
+        secs = time.perf_counter() - t0
+    return {"value": round(evals / secs, 2), "unit": "evals/s", "cores": cores, "evals": evals,
+            "s": round(secs, 2),
+            "sample": "SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first %d points "
+                      "of pairs 0..%d, one process per core, all at once" % (prefix, cores - 1)}
+
+
+def _oracle_job_ready(_):
+    from oracle import oracle as O   # noqa: F401  (loads the oracle library in the worker)
+    from paper_2204_09131_gb300 import synth   # noqa: F401
+    return True
+
+
+def cpu_baseline(pairs, decided_by_size=None, steps=1, prefix=12000, length=100000):
     """The oracle, single thread, on bounded samples of the workload.
 
     value: the step's decided windows divided by the oracle's extrapolated time for them --
@@ -470,6 +509,7 @@ def cpu_baseline(pairs, decided_by_size=None, steps=1, prefix=12000):
         out["value"] = out["measured_search"]["value"]
         out["sample"] = "oracle " + out["measured_search"]["sample"]
     out["config1_full"] = config1_full()
+    out["multicore"] = oracle_multicore(len(pairs), length, prefix)
     return out
 
 
@@ -863,7 +903,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pairs, st["decided_by_size"], args.steps)
+        cpu = cpu_baseline(pairs, st["decided_by_size"], args.steps, length=args.length)
         # the GPU's searches on the same prefix must return the oracle's windows
         td, bu = cpu.pop("_searches")
         got = api.isycos_search_queries(ctx, [(ids[0][0], ids[0][1], 0, 12000, dict(PARAMS, mode=0)),
