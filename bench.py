@@ -514,37 +514,46 @@ def cpu_baseline(pairs, decided_by_size=None, steps=1, prefix=12000, length=1000
 
 
 def reference_arm(args):
+    """The oracle as it stands, on the host's cores: each step runs its SYCOS_TD + SYCOS_BU on
+    the first 12,000 points of pairs 0 .. C-1 at once, one single-threaded process per usable
+    core (C of them, spawned and warmed up before the clock starts)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    pairs = make_pairs(0, 1, args.length)
-    x, y = pairs[0]
+    import multiprocessing as mp
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    cores = max(1, min(cores, 16))
+    prefix = 12000
+    jobs = [(p, args.length, prefix) for p in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_job_ready, range(cores))
 
-    def one_step():
-        """The oracle's SYCOS_TD + SYCOS_BU on the first 12,000 points of pair 0."""
-        from oracle import oracle as O
+        def one_step():
+            t0 = time.perf_counter()
+            evals = sum(pool.map(_oracle_search_job, jobs, chunksize=1))
+            dt = time.perf_counter() - t0
+            return {"value": round(evals / dt, 2), "unit": "evals/s", "cores": cores, "kind": "oracle",
+                    "host": host_info(),
+                    "sample": "oracle SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first "
+                              "%d points of pairs 0..%d, one process per core at once: %d window scores "
+                              "in %.1f s" % (prefix, cores - 1, evals, dt)}
+
+        for _ in range(args.warmup):   # untimed, like the other arm's warm-up steps
+            one_step()
+        vals = []
         t0 = time.perf_counter()
-        _, n1 = O.search_td(x[:12000], y[:12000], **PARAMS)
-        _, n2 = O.search_bu(x[:12000], y[:12000], **PARAMS)
-        dt = time.perf_counter() - t0
-        return {"value": round((n1 + n2) / dt, 2), "unit": "evals/s", "cores": 1, "kind": "oracle",
-                "host": host_info(),
-                "sample": "oracle SYCOS_TD + SYCOS_BU (pruning on, k=4, sizes 32-4096) on the first "
-                          "12000 points of pair 0: %d window scores in %.1f s" % (n1 + n2, dt)}
-
-    for _ in range(args.warmup):   # untimed, like the other arm's warm-up steps
-        one_step()
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(one_step())
-    ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+        for _ in range(args.steps):
+            vals.append(one_step())
+        ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     v = statistics.median([c["value"] for c in vals])
     line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "isycos-td-bu-64x100k", "pairs": 1, "length": 12000,
+            "config": {"workload": "isycos-td-bu-64x100k", "pairs": cores, "length": prefix,
                        "k": 4, "s_min": 32, "s_max": 4096, "pruning": 1},
             "cpu_baseline": dict(vals[-1], value=v),
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
