@@ -386,10 +386,9 @@ isycos_status isycos_get_tuning(isycos_ctx *ctx, int32_t k, uint32_t *sorted_buc
 #define ISYCOS_OPT_SERVE_SLOTS 3   /* serving: most queries admitted at once (default 64)   */
 #define ISYCOS_OPT_SERVE_QUEUE 4   /* serving: most queries waiting (default 100000)        */
 #define ISYCOS_OPT_LANES 5         /* searches: most engine lanes (host thread + stream +
-                                      work buffers), 1 .. 16 (default: 3/4 of the host cores,
-                                      at most 12); a call that mixes SYCOS_TD with other
-                                      queries adds up to a quarter as many lanes for the TD
-                                      queries                                               */
+                                      work buffers), 1 .. 16 (default: the host cores, at
+                                      most 16); a call that mixes SYCOS_TD with other
+                                      queries gives a quarter of them to the TD queries     */
 #define ISYCOS_OPT_ESTIMATOR 6     /* estimator of isycos_mi_windows, _points, _device and
                                       _plain: 0 Kraskov's second (Eq. KSGmi, default), 1
                                       Kraskov's first, psi(k) + psi(m) - <psi(n_x + 1) +

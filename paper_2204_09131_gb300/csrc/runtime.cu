@@ -597,7 +597,7 @@ isycos_status isycos_create(isycos_ctx **out, int32_t device, uint64_t mem_budge
     }
     {
         unsigned hw = std::thread::hardware_concurrency();
-        ctx->max_lanes = (int)std::max(1u, std::min(12u, hw * 3 / 4));
+        ctx->max_lanes = (int)std::max(1u, std::min((unsigned)kMaxLanes, hw));
         load_tunings(ctx);   // choices isycos_autotune stored for this GPU, if any
         Lane *L0 = nullptr;
         if (get_lane(ctx, 0, &L0) != ISYCOS_OK) {

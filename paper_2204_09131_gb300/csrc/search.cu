@@ -1525,15 +1525,16 @@ static isycos_status run_queries(isycos_ctx *ctx, int64_t n_q, const int32_t *xs
     // ones (latency-bound).  When both are present they get separate lanes: the TD lanes'
     // launches leave a quarter of the GPU's CTA slots free and the others run on
     // high-priority streams, so that their rounds overlap the large launches instead of
-    // waiting behind them.  The TD lanes, which mostly wait on their launches, come in
-    // addition to the lanes of the latency-bound queries.
+    // waiting behind them.  The TD lanes take a quarter of the lanes, the latency-bound
+    // queries the rest, so that the call keeps one host thread per lane.
     std::vector<SearchMachine *> thr, lat;
     for (SearchMachine *m : ms) (m->prm.mode == 0 ? thr : lat).push_back(m);
     const bool split = !thr.empty() && !lat.empty();
     int n_thr = 0, n_all = n_lanes;
     if (split) {
-        const int n_lat = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->max_lanes, ((int64_t)lat.size() + 3) / 4));
         n_thr = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, ctx->max_lanes / 4), ((int64_t)thr.size() + 3) / 4));
+        const int n_lat = (int)std::max<int64_t>(
+            1, std::min<int64_t>(std::max(1, ctx->max_lanes - n_thr), ((int64_t)lat.size() + 3) / 4));
         n_all = n_thr + n_lat;
     }
     std::vector<Lane *> lanes((size_t)n_all);
