@@ -98,36 +98,85 @@ __device__ __forceinline__ void ksg_block(Src s, int m, int base,
             bd[p][r] = kInf;
             bj[p][r] = 0;
         }
-    int j = 0;
-    for (; j + kUnroll <= m; j += kUnroll) {
-        float2 v[kUnroll];
+    // The first 32 candidates, while the lists fill, and those from 512 on, which rarely
+    // enter a list: in order, four at a time.
+    auto in_order = [&](int j, int jh) {
+        for (; j + kUnroll <= jh; j += kUnroll) {
+            float2 v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) v[u] = s[j + u];
-        float d[kUnroll][P];
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                d[u][p] = fmaxf(fabsf(xi[p] - v[u].x), fabsf(yi[p] - v[u].y));
-                any |= d[u][p] < bd[p][K1 - 1];
-            }
-        if (any) {
+            for (int u = 0; u < kUnroll; ++u) v[u] = s[j + u];
+            float d[kUnroll][P];
+            bool any = false;
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-                for (int p = 0; p < P; ++p)
-                    if (d[u][p] < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d[u][p], j + u);
+                for (int p = 0; p < P; ++p) {
+                    d[u][p] = fmaxf(fabsf(xi[p] - v[u].x), fabsf(yi[p] - v[u].y));
+                    any |= d[u][p] < bd[p][K1 - 1];
+                }
+            if (any) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        if (d[u][p] < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d[u][p], j + u);
+            }
         }
-    }
-    for (; j < m; ++j) {
-        const float2 v = s[j];
+        for (; j < jh; ++j) {
+            const float2 v = s[j];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float d = fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y));
+                if (d < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d, j);
+            }
+        }
+    };
+    in_order(0, min(m, 32));
+    // Candidates 32 .. 511 in chunks of 32: a lane marks the candidates closer than its
+    // list's last entry at the chunk's start (no other can enter: that entry only shrinks),
+    // then the lanes insert their marked candidates together, in increasing j, as many
+    // rounds as the most marked (a warp that inserted per candidate would run an insertion
+    // for nearly every one, since some lane's list takes it).
+    const int jc = min(m, 512);
+    for (int j0 = 32; j0 < jc; j0 += 32) {
+        const int n = min(32, jc - j0);
+        unsigned mk[P];
+        float t[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const float d = fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y));
-            if (d < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d, j);
+            mk[p] = 0u;
+            t[p] = bd[p][K1 - 1];
+        }
+        int u = 0;
+        for (; u + kUnroll <= n; u += kUnroll) {
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const float2 v = s[j0 + u + q];
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    mk[p] |= (fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y)) < t[p] ? 1u : 0u) << (u + q);
+            }
+        }
+        for (; u < n; ++u) {
+            const float2 v = s[j0 + u];
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                mk[p] |= (fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y)) < t[p] ? 1u : 0u) << u;
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            while (__any_sync(kFull, mk[p] != 0u)) {
+                if (mk[p] != 0u) {
+                    const int b = __ffs(mk[p]) - 1;
+                    mk[p] &= mk[p] - 1u;
+                    const float2 v = s[j0 + b];
+                    const float d = fmaxf(fabsf(xi[p] - v.x), fabsf(yi[p] - v.y));
+                    if (d < bd[p][K1 - 1]) list_insert<K1>(bd[p], bj[p], d, j0 + b);
+                }
+            }
         }
     }
+    in_order(jc, m);
 
     // a3: per-dimension distances to the neighbours.
     float dxm[P], dym[P];
@@ -163,7 +212,7 @@ __device__ __forceinline__ void ksg_block(Src s, int m, int base,
         cx[p] = 0;
         cy[p] = 0;
     }
-    j = 0;
+    int j = 0;
     for (; j + kUnroll <= m; j += kUnroll) {
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
