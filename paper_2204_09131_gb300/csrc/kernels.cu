@@ -243,14 +243,57 @@ __device__ __forceinline__ void visit1(const float4 *rec, const unsigned long lo
     if (d < bd[K1 - 1] || (d == bd[K1 - 1] && jj < bj[K1 - 1])) insert_lex<K1>(bd, bj, d, jj);
 }
 
-// Positions [a0, a1) of the order, every lane of the warp.
+// Positions base + q dir, q < n (n <= 32): every lane marks, in a mask, the candidates that
+// would enter its list as it stands (no other can enter later: its last entry only
+// decreases), then the lanes insert their own marked candidates together, as many rounds as
+// the most marked, instead of one warp-wide insertion per candidate that some lane takes.
+// (Used for the second half of the seeds, where most candidates enter no list; in the
+// outward extensions, eight at a time, the marking costs more than it saves.)
+template <int K1, bool Y>
+__device__ __forceinline__ void visit_masked(const float4 *rec, const unsigned long long *keys,
+                                             const float2 *s, float xi, float yi, float (&bd)[K1],
+                                             int (&bj)[K1], int base, int dir, int n) {
+    const float t = bd[K1 - 1];
+    const int tj = bj[K1 - 1];
+    unsigned mk = 0u;
+    int q = 0;
+    for (; q + 4 <= n; q += 4) {
+        float4 c[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) c[r] = cand<Y>(rec, keys, s, base + (q + r) * dir);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float d = fmaxf(fabsf(xi - c[r].x), fabsf(yi - c[r].y));
+            const bool in = d < t || (d == t && __float_as_int(c[r].z) < tj);
+            mk |= (in ? 1u : 0u) << (q + r);
+        }
+    }
+    for (; q < n; ++q) {
+        const float4 c = cand<Y>(rec, keys, s, base + q * dir);
+        const float d = fmaxf(fabsf(xi - c.x), fabsf(yi - c.y));
+        const bool in = d < t || (d == t && __float_as_int(c.z) < tj);
+        mk |= (in ? 1u : 0u) << q;
+    }
+    while (__any_sync(kFull, mk != 0u)) {
+        if (mk != 0u) {
+            const int b = __ffs(mk) - 1;
+            mk &= mk - 1u;
+            visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, base + b * dir);
+        }
+    }
+}
+
+// Positions [a0, a1) of the order, every lane of the warp: the first 32 in order (the lists
+// are still filling), the rest marked and inserted lane by lane.
 template <int K1, bool Y>
 __device__ __forceinline__ void visit_range(const float4 *rec, const unsigned long long *keys,
                                             const float2 *s, float xi, float yi, float (&bd)[K1],
                                             int (&bj)[K1], int a0, int a1) {
+    const int ah = min(a1, a0 + 32);
     int u = a0;
-    for (; u + 4 <= a1; u += 4) visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, u, 1);
-    for (; u < a1; ++u) visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, u);
+    for (; u + 4 <= ah; u += 4) visit4<K1, Y>(rec, keys, s, xi, yi, bd, bj, u, 1);
+    for (; u < ah; ++u) visit1<K1, Y>(rec, keys, s, xi, yi, bd, bj, u);
+    for (; u < a1; u += 32) visit_masked<K1, Y>(rec, keys, s, xi, yi, bd, bj, u, 1, min(32, a1 - u));
 }
 
 // Extend the scanned positions (L, R) outward, 8 at a time on each side, while the next
